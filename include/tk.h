@@ -1,0 +1,171 @@
+/*
+ * tk.h -- C ABI of libtk, the GB300 (sm_103a) implementation of the packed
+ * tensor-kernel method for l^p-regularised regression of
+ * F. Hibraj, "Efficient Tensor Kernel methods for sparse regression".
+ *
+ * Notation.  m is the (even) tensor order, the thesis's q; p = m/(m-1).
+ * n is the number of points the tensor is built over (all training points,
+ * or the n' Nystrom landmarks of Section 6).  d is the feature dimension.
+ * lambda = 1/gamma is the regularisation weight of the dual (Section 4,
+ * eq. dual_tensor_kernel written with 1/(2 gamma) = lambda/2).
+ *
+ * Packed layout (Section 5).  The order-m symmetric tensor K is stored as the
+ * N = C(n+m-1, m) entries whose indices are sorted, i_1 <= i_2 <= ... <= i_m,
+ * in the order of the thesis's nested loops: lexicographic, i_1 slowest and
+ * i_m fastest.  Offset 0 is (0,...,0); offset N-1 is (n-1,...,n-1).  A "row"
+ * is the run of entries sharing i_1..i_{m-1}; it holds n - i_{m-1} entries.
+ * Entry types: TK_F64 (8 B), TK_F32 (4 B), TK_BF16 (2 B, round-to-nearest-even
+ * from the FP32 accumulator).
+ *
+ * Conventions.
+ *   - Every function returns TK_OK (0) or a TK_E* code; tk_last_error() gives
+ *     a message for the calling thread's last failure.
+ *   - The caller owns all memory.  Unless marked "host", pointers are device
+ *     pointers.  The library allocates no device memory on any call path
+ *     below except where stated; scratch space is sized by the matching
+ *     *_workspace_size call and passed in as `work`.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device calls are asynchronous on that stream unless noted.
+ *   - Device buffers must be 16-byte aligned (every cudaMalloc / PyTorch
+ *     allocation is).
+ *   - Results are deterministic: no floating-point atomics; every reduction
+ *     runs in a fixed order.
+ */
+#ifndef TK_H
+#define TK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+enum {
+    TK_OK = 0,
+    TK_EINVAL = 1,       /* bad argument (sizes, dtype, order, pointer, alignment) */
+    TK_EOVERFLOW = 2,    /* N or an offset does not fit the 64-bit index space */
+    TK_ENOMEM = 3,       /* the workspace passed in is smaller than required */
+    TK_ECUDA = 4,        /* a CUDA runtime call failed (message has the CUDA error) */
+    TK_ENOTCONV = 5,     /* the solver stopped at max_iter before reaching tol */
+    TK_ETIMEOUT = 6,     /* a bounded device-side wait ran out (see tk_status_read) */
+    TK_EUNSUPPORTED = 7  /* valid input outside what this build implements */
+};
+
+enum { TK_F64 = 0, TK_F32 = 1, TK_BF16 = 2 };
+
+/* Feature maps of the tensor kernels of Section 4:
+ *   TK_FEAT_LINEAR  k = sum_j prod_l x'_{l,j}           (linear tensor kernel)
+ *   TK_FEAT_POLY    k = (sum_j prod_l x'_{l,j})^degree   (polynomial tensor kernel,
+ *                                                         eq. poly_tensor)
+ *   TK_FEAT_EXP     k = exp(sum_j prod_l x'_{l,j})       (exponential tensor kernel) */
+enum { TK_FEAT_LINEAR = 0, TK_FEAT_POLY = 1, TK_FEAT_EXP = 2 };
+
+/* Dual solver methods (the thesis does not state its algorithm). */
+enum { TK_NEWTON_CG = 0, TK_GD_BT = 1 };
+
+/* Largest supported order and point count of the device contraction. */
+#define TK_MAX_ORDER 8
+#define TK_MAX_POINTS 1024
+
+const char *tk_last_error(void);
+const char *tk_version(void);
+
+/* ------------------------------------------------------------ layout (host) */
+
+/* N = C(n+m-1, m): the number of stored entries of the order-m symmetric
+ * tensor over n points (Section 5: b_matrix, b_cube, b_tensor4 are m = 2,3,4).
+ * Returns -1 if m < 1, n < 0, or N (or N*8) overflows int64. */
+int64_t tk_packed_size(int m, int64_t n);
+
+/* Bytes of N entries of `dtype`; -1 on error. */
+int64_t tk_packed_bytes(int m, int64_t n, int dtype);
+
+/* Offset of the sorted tuple idx_host[0..m-1] (host) in the packed order
+ * (Section 5, eqs. index_2d, v3d, v4d and their extension to any m).  The
+ * tuple must be non-decreasing with entries in [0, n): else TK_EINVAL. */
+int tk_rank(int m, int64_t n, const int32_t *idx_host, int64_t *off_host);
+
+/* Inverse of tk_rank: the sorted tuple stored at `off` (0 <= off < N). */
+int tk_unrank(int m, int64_t n, int64_t off, int32_t *idx_host);
+
+/* First row start at or after `off` (a row start is an offset whose tuple
+ * has i_{m-1} == i_m); returns N when off > last row start.  Used to cut the
+ * packed array into row-aligned shards. */
+int tk_row_align(int m, int64_t n, int64_t off, int64_t *row_off_host);
+
+/* ------------------------------------------------------------ build */
+
+/* Packed build (Section 4 tensor kernel, stored as in Section 5):
+ *   K[o] = k(x_{i_1}, ..., x_{i_m}) for the sorted tuple i at offset o.
+ * X: n x d row-major FP64 (device).  K: N entries of storage_dtype (device,
+ * caller-allocated with tk_packed_bytes bytes).  Accumulation is FP64 for
+ * TK_F64 storage and FP32 otherwise; TK_BF16 rounds the FP32 result to
+ * nearest-even.  `degree` is used by TK_FEAT_POLY only.  No workspace. */
+int tk_build_packed(int m, int64_t n, int64_t d, const double *X, int feat,
+                    int degree, int storage_dtype, void *K, void *stream);
+
+/* Same for the offsets [off_lo, off_hi) only: K_range[o - off_lo] = K[o].
+ * Lets a shard of the packed array be built on its own device. */
+int tk_build_packed_range(int m, int64_t n, int64_t d, const double *X, int feat,
+                          int degree, int storage_dtype, int64_t off_lo,
+                          int64_t off_hi, void *K_range, void *stream);
+
+/* ------------------------------------------------------------ contraction */
+
+/* Bytes of workspace tk_contract / tk_objective need for (m, n, B). */
+size_t tk_contract_workspace_size(int m, int64_t n, int64_t B);
+
+/* Contractions of the symmetric tensor over its packed entries, each equal to
+ * the full sum over all n^m index tuples of Section 4, eq. dual_tensor_kernel:
+ *
+ *   r = m-1:  G[b] = K[A_b^{m-1}]   (n-vector; K[a^{m-1}]_l = sum over i_2..i_m of
+ *                                     K_{l,i_2..i_m} a_{i_2} ... a_{i_m})
+ *             S[b] = K[A_b^m]       (optional, S may be NULL)
+ *   r = m-2:  G[b] = K[A_b^{m-2}, V_b] (the Hessian-vector product of
+ *             K[a^m]/(m(m-1)); V required)
+ *
+ * G excludes the factor m of the gradient m K[a^{m-1}]; callers scale.
+ * A, V, G: B x n row-major, vec_dtype TK_F64 or TK_F32.  S: B FP64 values.
+ * Arithmetic: FP64 for TK_F64 storage; FP32 for TK_F32 / TK_BF16 storage with
+ * the cross-block reduction and S in FP64.  Each packed entry is read from
+ * HBM once per pass; B > 1 loops over the batch (see tk_contract_batched for
+ * one pass over all B).  Asynchronous; errors that only the device can see
+ * (a bounded wait that ran out) are recorded in `work` and returned by
+ * tk_status_read. */
+int tk_contract(int m, int64_t n, int storage_dtype, const void *K, int64_t B,
+                int vec_dtype, const void *A, int r, const void *V, void *G,
+                double *S, void *work, size_t work_bytes, void *stream);
+
+/* Same over the row-aligned offset range [off_lo, off_hi) (see tk_row_align);
+ * K_range points at the entry of offset off_lo.  G and S receive the partial
+ * sums over that range, so that shards on several devices add up to the full
+ * contraction. */
+int tk_contract_range(int m, int64_t n, int storage_dtype, const void *K_range,
+                      int64_t off_lo, int64_t off_hi, int64_t B, int vec_dtype,
+                      const void *A, int r, const void *V, void *G, double *S,
+                      void *work, size_t work_bytes, void *stream);
+
+/* Reads (and clears) the device-side status word of a workspace: TK_OK, or
+ * TK_ETIMEOUT if a bounded wait of an earlier call on it ran out.  Synchronises
+ * `stream`. */
+int tk_status_read(void *work, void *stream);
+
+/* ------------------------------------------------------------ dual objective */
+
+/* Dual objective and gradient (Section 4, eqs. dual_tensor_kernel and jq, with
+ * lambda = 1/gamma), in FP64 on the device:
+ *   F[b]     = K[A_b^m]/m + (lambda_b/2) |A_b|^2 - <y, A_b>
+ *   grad[b]  = K[A_b^{m-1}] + lambda_b A_b - y        (optional, B x n FP64)
+ *   gnorm[b] = |grad[b]|_2                            (optional)
+ * A: B x n FP64, y: n FP64, lambda: B FP64 (all device).  One contraction pass. */
+int tk_objective(int m, int64_t n, int storage_dtype, const void *K, int64_t B,
+                 const double *A, const double *y, const double *lambda, double *F,
+                 double *grad, double *gnorm, void *work, size_t work_bytes,
+                 void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TK_H */

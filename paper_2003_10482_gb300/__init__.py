@@ -1,0 +1,251 @@
+"""Python binding of libtk (include/tk.h): packed tensor-kernel l^p regression on GB300.
+
+Thin argument marshalling over the C ABI, with the same function names.  Every
+computation runs in the CUDA library; PyTorch only provides device memory and
+streams.  There is no CPU fallback: if ``libtk.so`` has not been built the
+import of the library fails loudly.
+
+Tensor conventions: device tensors, contiguous; storage dtypes torch.float64 /
+torch.float32 / torch.bfloat16 map to TK_F64 / TK_F32 / TK_BF16.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtk.so")
+
+TK_OK, TK_EINVAL, TK_EOVERFLOW, TK_ENOMEM, TK_ECUDA, TK_ENOTCONV, TK_ETIMEOUT, TK_EUNSUPPORTED = range(8)
+TK_F64, TK_F32, TK_BF16 = 0, 1, 2
+TK_FEAT_LINEAR, TK_FEAT_POLY, TK_FEAT_EXP = 0, 1, 2
+TK_NEWTON_CG, TK_GD_BT = 0, 1
+
+_DT = {torch.float64: TK_F64, torch.float32: TK_F32, torch.bfloat16: TK_BF16}
+_TORCH = {TK_F64: torch.float64, TK_F32: torch.float32, TK_BF16: torch.bfloat16}
+_NAMES = {"f64": TK_F64, "f32": TK_F32, "bf16": TK_BF16}
+_FEAT = {"linear": TK_FEAT_LINEAR, "poly": TK_FEAT_POLY, "exp": TK_FEAT_EXP}
+
+
+class TKError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libtk error {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libtk.so (built by ``build_lib.build()``); raises if it is absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(
+                    f"{LIB_PATH} is missing: build it with "
+                    "`python -m paper_2003_10482_gb300.build_lib` (no CPU fallback exists)")
+            L = ctypes.CDLL(LIB_PATH)
+            _declare(L)
+            _lib = L
+    return _lib
+
+
+def _declare(L):
+    i32, i64, u64, sz, dbl = ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_size_t, ctypes.c_double
+    P = ctypes.c_void_p
+    sig = {
+        "tk_last_error": (ctypes.c_char_p, []),
+        "tk_version": (ctypes.c_char_p, []),
+        "tk_packed_size": (i64, [i32, i64]),
+        "tk_packed_bytes": (i64, [i32, i64, i32]),
+        "tk_rank": (i32, [i32, i64, P, P]),
+        "tk_unrank": (i32, [i32, i64, i64, P]),
+        "tk_row_align": (i32, [i32, i64, i64, P]),
+        "tk_build_packed": (i32, [i32, i64, i64, P, i32, i32, i32, P, P]),
+        "tk_build_packed_range": (i32, [i32, i64, i64, P, i32, i32, i32, i64, i64, P, P]),
+        "tk_contract_workspace_size": (sz, [i32, i64, i64]),
+        "tk_contract": (i32, [i32, i64, i32, P, i64, i32, P, i32, P, P, P, P, sz, P]),
+        "tk_contract_range": (i32, [i32, i64, i32, P, i64, i64, i64, i32, P, i32, P, P, P, P, sz, P]),
+        "tk_status_read": (i32, [P, P]),
+        "tk_objective": (i32, [i32, i64, i32, P, i64, P, P, P, P, P, P, P, sz, P]),
+    }
+    for name, (res, args) in sig.items():
+        if hasattr(L, name):
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+
+
+def exported_symbols():
+    """Names of the tk_* functions declared in include/tk.h."""
+    import re
+    hdr = os.path.join(os.path.dirname(_HERE), "include", "tk.h")
+    with open(hdr) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"\b(tk_[a-z0-9_]+)\s*\(", text)))
+
+
+def _check(rc):
+    if rc != TK_OK:
+        raise TKError(rc, lib().tk_last_error().decode())
+
+
+def _p(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def dtype_code(dt) -> int:
+    if isinstance(dt, str):
+        return _NAMES[dt]
+    if isinstance(dt, int):
+        return dt
+    return _DT[dt]
+
+
+def torch_dtype(code) -> torch.dtype:
+    return _TORCH[dtype_code(code)]
+
+
+# ------------------------------------------------------------------ layout (host)
+def tk_packed_size(m: int, n: int) -> int:
+    v = lib().tk_packed_size(m, n)
+    if v < 0:
+        raise TKError(TK_EOVERFLOW, f"C(n+m-1, m) invalid for m={m}, n={n}")
+    return int(v)
+
+
+def tk_packed_bytes(m: int, n: int, dtype) -> int:
+    v = lib().tk_packed_bytes(m, n, dtype_code(dtype))
+    if v < 0:
+        raise TKError(TK_EINVAL, "bad size or dtype")
+    return int(v)
+
+
+def tk_rank(m: int, n: int, idx) -> int:
+    a = (ctypes.c_int32 * m)(*[int(i) for i in idx])
+    off = ctypes.c_int64()
+    _check(lib().tk_rank(m, n, a, ctypes.byref(off)))
+    return off.value
+
+
+def tk_unrank(m: int, n: int, off: int) -> list[int]:
+    a = (ctypes.c_int32 * m)()
+    _check(lib().tk_unrank(m, n, off, a))
+    return list(a)
+
+
+def tk_row_align(m: int, n: int, off: int) -> int:
+    r = ctypes.c_int64()
+    _check(lib().tk_row_align(m, n, off, ctypes.byref(r)))
+    return r.value
+
+
+# ------------------------------------------------------------------ workspace
+_ws_cache: dict = {}
+
+
+def workspace(m: int, n: int, B: int = 1, device=None) -> torch.Tensor:
+    """A cached device workspace large enough for contractions of (m, n, B)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    with torch.cuda.device(dev):
+        need = int(lib().tk_contract_workspace_size(m, n, B))
+    if need == 0:
+        raise TKError(TK_EINVAL, lib().tk_last_error().decode())
+    key = dev.index
+    t = _ws_cache.get(key)
+    if t is None or t.numel() < need:
+        t = torch.zeros(need, dtype=torch.uint8, device=dev)
+        _ws_cache[key] = t
+    return t
+
+
+def tk_status_read(work: torch.Tensor, stream=None) -> int:
+    return int(lib().tk_status_read(_p(work), _stream(stream)))
+
+
+# ------------------------------------------------------------------ build
+def tk_build_packed(X: torch.Tensor, m: int, storage="f32", feat="linear", degree: int = 1,
+                    K: torch.Tensor | None = None, off_lo: int | None = None,
+                    off_hi: int | None = None, stream=None) -> torch.Tensor:
+    """Packed order-m tensor kernel of the rows of X (n x d, FP64, device)."""
+    assert X.is_cuda and X.dtype == torch.float64 and X.dim() == 2
+    X = X.contiguous()
+    n, d = X.shape
+    code = dtype_code(storage)
+    N = tk_packed_size(m, n)
+    lo = 0 if off_lo is None else off_lo
+    hi = N if off_hi is None else off_hi
+    if K is None:
+        K = torch.empty(hi - lo, dtype=_TORCH[code], device=X.device)
+    assert K.numel() >= hi - lo and K.dtype == _TORCH[code]
+    f = _FEAT[feat] if isinstance(feat, str) else int(feat)
+    if off_lo is None and off_hi is None:
+        _check(lib().tk_build_packed(m, n, d, _p(X), f, degree, code, _p(K), _stream(stream)))
+    else:
+        _check(lib().tk_build_packed_range(m, n, d, _p(X), f, degree, code, lo, hi, _p(K),
+                                           _stream(stream)))
+    return K
+
+
+# ------------------------------------------------------------------ contraction
+def tk_contract(K: torch.Tensor, m: int, n: int, A: torch.Tensor, r: int | None = None,
+                V: torch.Tensor | None = None, G: torch.Tensor | None = None,
+                S: torch.Tensor | None = None, off_lo: int | None = None,
+                off_hi: int | None = None, work: torch.Tensor | None = None, stream=None):
+    """G = K[A^{m-1}] and S = K[A^m] (r = m-1), or G = K[A^{m-2}, V] (r = m-2).
+
+    A (and V): (n,) or (B, n) FP64/FP32 device tensors.  Returns (G, S) with G
+    shaped like A and S a (B,) FP64 tensor (None for r = m-2)."""
+    r = m - 1 if r is None else r
+    squeeze = A.dim() == 1
+    A2 = A.reshape(-1, n).contiguous()
+    B = A2.shape[0]
+    vdt = dtype_code(A2.dtype)
+    V2 = None if V is None else V.reshape(B, n).to(A2.dtype).contiguous()
+    if G is None:
+        G = torch.empty_like(A2)
+    if S is None and r == m - 1:
+        S = torch.empty(B, dtype=torch.float64, device=A.device)
+    if work is None:
+        work = workspace(m, n, B, A.device)
+    sc = dtype_code(K.dtype)
+    if off_lo is None and off_hi is None:
+        rc = lib().tk_contract(m, n, sc, _p(K), B, vdt, _p(A2), r, _p(V2), _p(G), _p(S),
+                               _p(work), work.numel(), _stream(stream))
+    else:
+        rc = lib().tk_contract_range(m, n, sc, _p(K), off_lo, off_hi, B, vdt, _p(A2), r,
+                                     _p(V2), _p(G), _p(S), _p(work), work.numel(),
+                                     _stream(stream))
+    _check(rc)
+    if squeeze:
+        G = G.reshape(n)
+    return G, (S if r == m - 1 else None)
+
+
+def tk_objective(K: torch.Tensor, m: int, n: int, A: torch.Tensor, y: torch.Tensor,
+                 lam, work: torch.Tensor | None = None, stream=None):
+    """(F, grad, gnorm) of the dual objective for each row of A (FP64)."""
+    A2 = A.reshape(-1, n).to(torch.float64).contiguous()
+    B = A2.shape[0]
+    lam_t = torch.as_tensor(lam, dtype=torch.float64, device=A.device).reshape(-1)
+    if lam_t.numel() == 1 and B > 1:
+        lam_t = lam_t.expand(B).contiguous()
+    F = torch.empty(B, dtype=torch.float64, device=A.device)
+    gn = torch.empty(B, dtype=torch.float64, device=A.device)
+    grad = torch.empty_like(A2)
+    if work is None:
+        work = workspace(m, n, B, A.device)
+    _check(lib().tk_objective(m, n, dtype_code(K.dtype), _p(K), B, _p(A2),
+                              _p(y.to(torch.float64).contiguous()), _p(lam_t), _p(F), _p(grad),
+                              _p(gn), _p(work), work.numel(), _stream(stream)))
+    return F, grad.reshape(A.shape), gn

@@ -1,0 +1,281 @@
+// C ABI entry points of libtk: argument checks, workspace layout, launches.
+#include <stdarg.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "tk_internal.h"
+
+namespace tk {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int fail(int code, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+  set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+  return TK_ECUDA;
+}
+
+int dev_info(DevInfo *out) {
+  static thread_local int cached_dev = -1;
+  static thread_local DevInfo cached;
+  int dev = 0;
+  TK_CUDA_CHECK(cudaGetDevice(&dev));
+  if (dev != cached_dev) {
+    TK_CUDA_CHECK(cudaDeviceGetAttribute(&cached.sms, cudaDevAttrMultiProcessorCount, dev));
+    TK_CUDA_CHECK(cudaDeviceGetAttribute(&cached.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cached_dev = dev;
+  }
+  *out = cached;
+  return TK_OK;
+}
+
+// N = C(n+m-1, m) with an overflow guard: N * 16 must stay below 2^63 so that
+// every partial product of the exact binomial evaluation fits.
+static int64_t packed_size_checked(int m, int64_t n) {
+  if (m < 1 || m > 16 || n < 0) return -1;
+  if (n == 0) return 0;
+  // evaluate in long double first to reject sizes whose binomial overflows
+  long double c = 1.0L;
+  for (int i = 0; i < m; ++i) c = c * (long double)(n + m - 1 - i) / (long double)(i + 1);
+  if (c * 16.0L > 9.0e18L) return -1;
+  return multiset(n, m);
+}
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+static int check_order_points(int m, int64_t n) {
+  if (m < 2 || m > TK_MAX_ORDER) return fail(TK_EINVAL, "order m=%d outside [2, %d]", m, TK_MAX_ORDER);
+  if (n < 1) return fail(TK_EINVAL, "n=%lld must be >= 1", (long long)n);
+  if (n > TK_MAX_POINTS) return fail(TK_EUNSUPPORTED, "n=%lld exceeds %d", (long long)n, TK_MAX_POINTS);
+  if (packed_size_checked(m, n) < 0) return fail(TK_EOVERFLOW, "C(n+m-1, m) overflows");
+  return TK_OK;
+}
+
+static bool is_row_start(int m, int64_t n, int64_t off, int64_t N) {
+  if (off == N) return true;
+  int32_t t[16];
+  unrank(m, n, off, t);
+  return t[m - 1] == t[m - 2];
+}
+
+}  // namespace tk
+
+using namespace tk;
+
+extern "C" {
+
+const char *tk_last_error(void) { return g_err; }
+
+const char *tk_version(void) { return "tk 0.1 (sm_103a)"; }
+
+int64_t tk_packed_size(int m, int64_t n) { return packed_size_checked(m, n); }
+
+int64_t tk_packed_bytes(int m, int64_t n, int dtype) {
+  if (dtype < TK_F64 || dtype > TK_BF16) return -1;
+  int64_t N = packed_size_checked(m, n);
+  if (N < 0) return -1;
+  return N * dtype_size(dtype);
+}
+
+int tk_rank(int m, int64_t n, const int32_t *idx, int64_t *off) {
+  if (!idx || !off) return fail(TK_EINVAL, "tk_rank: NULL pointer");
+  if (packed_size_checked(m, n) < 0 || n < 1) return fail(TK_EINVAL, "tk_rank: bad m=%d / n", m);
+  for (int j = 0; j < m; ++j) {
+    if (idx[j] < 0 || idx[j] >= n || (j > 0 && idx[j] < idx[j - 1]))
+      return fail(TK_EINVAL, "tk_rank: tuple is not sorted within [0, n)");
+  }
+  *off = rank(m, n, idx);
+  return TK_OK;
+}
+
+int tk_unrank(int m, int64_t n, int64_t off, int32_t *idx) {
+  if (!idx) return fail(TK_EINVAL, "tk_unrank: NULL pointer");
+  int64_t N = packed_size_checked(m, n);
+  if (N < 0 || n < 1) return fail(TK_EINVAL, "tk_unrank: bad m=%d / n", m);
+  if (off < 0 || off >= N) return fail(TK_EINVAL, "tk_unrank: offset outside [0, N)");
+  unrank(m, n, off, idx);
+  return TK_OK;
+}
+
+int tk_row_align(int m, int64_t n, int64_t off, int64_t *row_off) {
+  if (!row_off) return fail(TK_EINVAL, "tk_row_align: NULL pointer");
+  int64_t N = packed_size_checked(m, n);
+  if (N < 0 || n < 1 || m < 2) return fail(TK_EINVAL, "tk_row_align: bad m=%d / n", m);
+  if (off < 0 || off > N) return fail(TK_EINVAL, "tk_row_align: offset outside [0, N]");
+  if (off == N) {
+    *row_off = N;
+    return TK_OK;
+  }
+  int32_t t[16];
+  unrank(m, n, off, t);
+  *row_off = (t[m - 1] == t[m - 2]) ? off : off + (n - t[m - 1]);
+  return TK_OK;
+}
+
+size_t tk_contract_workspace_size(int m, int64_t n, int64_t B) {
+  (void)B;
+  if (check_order_points(m, n) != TK_OK) return 0;
+  DevInfo di;
+  if (dev_info(&di) != TK_OK) return 0;
+  // up to 2 blocks per SM
+  return sizeof(WsHeader) + contract_part_bytes((int)n, 2 * di.sms);
+}
+
+static int contract_impl(int m, int64_t n, int storage, const void *K, int64_t off_lo, int64_t off_hi,
+                         int64_t B, int vec_dtype, const void *A, int r, const void *V, void *G, double *S,
+                         void *work, size_t work_bytes, void *stream) {
+  int rc = check_order_points(m, n);
+  if (rc != TK_OK) return rc;
+  if (storage < TK_F64 || storage > TK_BF16) return fail(TK_EINVAL, "bad storage dtype %d", storage);
+  if (vec_dtype != TK_F64 && vec_dtype != TK_F32) return fail(TK_EINVAL, "bad vector dtype %d", vec_dtype);
+  if (r != m - 1 && r != m - 2) return fail(TK_EINVAL, "r=%d must be m-1 or m-2", r);
+  if (r == m - 2 && !V) return fail(TK_EINVAL, "r = m-2 needs the direction V");
+  if (B < 0) return fail(TK_EINVAL, "B < 0");
+  if (B == 0) return TK_OK;
+  if (!A || !G || !work) return fail(TK_EINVAL, "NULL A, G or workspace");
+  const int64_t N = multiset(n, m);
+  if (off_lo < 0 || off_hi > N || off_lo > off_hi) return fail(TK_EINVAL, "range outside [0, N]");
+  if (!is_row_start(m, n, off_lo, N) || !is_row_start(m, n, off_hi, N))
+    return fail(TK_EINVAL, "range ends must be row starts (tk_row_align)");
+  if (off_hi > off_lo && !K) return fail(TK_EINVAL, "NULL K");
+  if (!aligned16(K) || !aligned16(work)) return fail(TK_EINVAL, "K and work must be 16-byte aligned");
+  DevInfo di;
+  rc = dev_info(&di);
+  if (rc != TK_OK) return rc;
+  const size_t need = sizeof(WsHeader) + contract_part_bytes((int)n, 2 * di.sms);
+  if (work_bytes < need) return fail(TK_ENOMEM, "workspace %zu < %zu bytes", work_bytes, need);
+
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int vs = vec_dtype == TK_F64 ? 8 : 4;
+  unsigned char *wsb = reinterpret_cast<unsigned char *>(work);
+  for (int64_t b = 0; b < B; ++b) {
+    ContractArgs a;
+    memset(&a, 0, sizeof(a));
+    a.m = m;
+    a.n = (int)n;
+    a.storage = storage;
+    a.K = K;
+    a.off_lo = off_lo;
+    a.off_hi = off_hi;
+    a.vec_dtype = vec_dtype;
+    a.alpha = reinterpret_cast<const unsigned char *>(A) + b * n * vs;
+    a.v = (r == m - 2) ? reinterpret_cast<const unsigned char *>(V) + b * n * vs : nullptr;
+    a.part = reinterpret_cast<double *>(wsb + sizeof(WsHeader));
+    a.status = reinterpret_cast<int *>(wsb);
+    int grid = 0;
+    rc = contract_pass(a, &grid, st);
+    if (rc != TK_OK) return rc;
+    FinalizeArgs f;
+    memset(&f, 0, sizeof(f));
+    f.mode = (r == m - 1) ? 0 : 1;
+    f.m = m;
+    f.n = (int)n;
+    f.grid = grid;
+    f.part = a.part;
+    f.out_dtype = vec_dtype;
+    f.G = reinterpret_cast<unsigned char *>(G) + b * n * vs;
+    f.S = (S && r == m - 1) ? S + b : nullptr;
+    rc = contract_finalize(f, st);
+    if (rc != TK_OK) return rc;
+  }
+  return TK_OK;
+}
+
+int tk_contract(int m, int64_t n, int storage, const void *K, int64_t B, int vec_dtype, const void *A, int r,
+                const void *V, void *G, double *S, void *work, size_t work_bytes, void *stream) {
+  int64_t N = packed_size_checked(m, n);
+  if (N < 0) return fail(TK_EOVERFLOW, "C(n+m-1, m) overflows");
+  return contract_impl(m, n, storage, K, 0, N, B, vec_dtype, A, r, V, G, S, work, work_bytes, stream);
+}
+
+int tk_contract_range(int m, int64_t n, int storage, const void *K_range, int64_t off_lo, int64_t off_hi,
+                      int64_t B, int vec_dtype, const void *A, int r, const void *V, void *G, double *S,
+                      void *work, size_t work_bytes, void *stream) {
+  return contract_impl(m, n, storage, K_range, off_lo, off_hi, B, vec_dtype, A, r, V, G, S, work, work_bytes,
+                       stream);
+}
+
+int tk_status_read(void *work, void *stream) {
+  if (!work) return fail(TK_EINVAL, "NULL workspace");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  WsHeader h;
+  TK_CUDA_CHECK(cudaMemcpyAsync(&h, work, sizeof(h), cudaMemcpyDeviceToHost, st));
+  TK_CUDA_CHECK(cudaStreamSynchronize(st));
+  if (h.status != TK_OK) {
+    int code = h.status;
+    TK_CUDA_CHECK(cudaMemsetAsync(work, 0, sizeof(WsHeader), st));
+    TK_CUDA_CHECK(cudaStreamSynchronize(st));
+    return fail(code, "device status %d (site %d)", code, h.where);
+  }
+  return TK_OK;
+}
+
+int tk_objective(int m, int64_t n, int storage, const void *K, int64_t B, const double *A, const double *y,
+                 const double *lambda, double *F, double *grad, double *gnorm, void *work, size_t work_bytes,
+                 void *stream) {
+  int rc = check_order_points(m, n);
+  if (rc != TK_OK) return rc;
+  if (storage < TK_F64 || storage > TK_BF16) return fail(TK_EINVAL, "bad storage dtype %d", storage);
+  if (B < 0) return fail(TK_EINVAL, "B < 0");
+  if (B == 0) return TK_OK;
+  if (!K || !A || !y || !lambda || !work) return fail(TK_EINVAL, "NULL pointer");
+  if (!aligned16(K) || !aligned16(work)) return fail(TK_EINVAL, "K and work must be 16-byte aligned");
+  DevInfo di;
+  rc = dev_info(&di);
+  if (rc != TK_OK) return rc;
+  const size_t need = sizeof(WsHeader) + contract_part_bytes((int)n, 2 * di.sms);
+  if (work_bytes < need) return fail(TK_ENOMEM, "workspace %zu < %zu bytes", work_bytes, need);
+  const int64_t N = multiset(n, m);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  unsigned char *wsb = reinterpret_cast<unsigned char *>(work);
+  for (int64_t b = 0; b < B; ++b) {
+    ContractArgs a;
+    memset(&a, 0, sizeof(a));
+    a.m = m;
+    a.n = (int)n;
+    a.storage = storage;
+    a.K = K;
+    a.off_lo = 0;
+    a.off_hi = N;
+    a.vec_dtype = TK_F64;
+    a.alpha = A + b * n;
+    a.part = reinterpret_cast<double *>(wsb + sizeof(WsHeader));
+    a.status = reinterpret_cast<int *>(wsb);
+    int grid = 0;
+    rc = contract_pass(a, &grid, st);
+    if (rc != TK_OK) return rc;
+    FinalizeArgs f;
+    memset(&f, 0, sizeof(f));
+    f.mode = 2;
+    f.m = m;
+    f.n = (int)n;
+    f.grid = grid;
+    f.part = a.part;
+    f.alpha = A + b * n;
+    f.y = y;
+    f.lambda = lambda + b;
+    f.F = F ? F + b : nullptr;
+    f.grad = grad ? grad + b * n : nullptr;
+    f.gnorm = gnorm ? gnorm + b : nullptr;
+    rc = contract_finalize(f, st);
+    if (rc != TK_OK) return rc;
+  }
+  return TK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,12 @@
+// Instantiations of the packed contraction kernel for f64 storage.
+#include "tk_contract_impl.cuh"
+
+namespace tk {
+
+int contract_launch_f64(const KParams &kp, bool dual, int nc, int grid, int threads, size_t smem,
+                          cudaStream_t st) {
+  return dual ? launch_typed<double, double, true>(kp, nc, grid, threads, smem, st)
+              : launch_typed<double, double, false>(kp, nc, grid, threads, smem, st);
+}
+
+}  // namespace tk

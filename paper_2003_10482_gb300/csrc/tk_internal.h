@@ -1,0 +1,85 @@
+// Internal declarations shared by the translation units of libtk.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/tk.h"
+#include "tk_core.h"
+
+namespace tk {
+
+// thread-local last error message (tk_last_error)
+void set_error(const char *fmt, ...);
+int fail(int code, const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define TK_CUDA_CHECK(call)                                     \
+  do {                                                          \
+    cudaError_t e__ = (call);                                   \
+    if (e__ != cudaSuccess) return ::tk::cuda_fail(e__, #call); \
+  } while (0)
+
+// Layout of every workspace: a 256-byte header (status word and reserved
+// counters) followed by the per-block partial sums of the contraction.
+struct WsHeader {
+  int status;        // TK_OK or TK_ETIMEOUT, set by kernels, read by tk_status_read
+  int where;         // which wait ran out (diagnostic)
+  int pad[62];
+};
+static_assert(sizeof(WsHeader) == 256, "header size");
+
+// Device properties cached per device.
+struct DevInfo {
+  int sms;
+  int smem_optin;  // max dynamic shared memory per block
+};
+int dev_info(DevInfo *out);
+
+// One contraction pass of the single-vector kernel.
+struct ContractArgs {
+  int m;
+  int n;
+  int storage;      // TK_F64 / TK_F32 / TK_BF16
+  const void *K;    // entry off_lo
+  int64_t off_lo, off_hi;
+  int vec_dtype;    // dtype of alpha / v
+  const void *alpha;
+  const void *v;    // non-NULL: dual pass (HVP)
+  double *part;     // per-block partials (workspace)
+  int *status;      // workspace status word
+  // tuning (0 = default)
+  int warps;
+  int slot_log2;
+  int ns_log2;
+  int ctas_per_sm;
+};
+
+// Launch the main pass; the partial sums land in args.part (layout
+// part[block][vec][n + 2]: vec 0 = value, vec 1 = derivative; entry n = S).
+int contract_pass(const ContractArgs &a, int *grid_out, cudaStream_t st);
+
+// Sum the per-block partials of one pass into outputs (FP64, fixed order).
+//   mode 0: G = value part (vec_dtype), S
+//   mode 1: G = derivative part / (m-1)  (HVP)
+//   mode 2: objective: F, grad (FP64), gnorm with alpha/y/lambda
+struct FinalizeArgs {
+  int mode;
+  int m, n, grid;
+  const double *part;
+  int out_dtype;
+  void *G;
+  double *S;
+  const double *alpha;  // mode 2
+  const double *y;
+  const double *lambda;
+  double *F;
+  double *grad;
+  double *gnorm;
+};
+int contract_finalize(const FinalizeArgs &f, cudaStream_t st);
+
+size_t contract_part_bytes(int n, int grid);
+int contract_default_grid();
+
+}  // namespace tk

@@ -1,0 +1,76 @@
+"""Host-side checks of libtk that need no GPU: the library loads, exports every
+symbol include/tk.h declares, and its layout helpers agree with the oracle."""
+import ctypes
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+
+tk = pytest.importorskip("paper_2003_10482_gb300")
+
+
+@pytest.fixture(scope="module")
+def L():
+    try:
+        return tk.lib()
+    except ImportError:
+        from paper_2003_10482_gb300 import build_lib
+        build_lib.build()
+        return tk.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    declared = tk.exported_symbols()
+    assert "tk_contract" in declared and "tk_build_packed" in declared
+    out = subprocess.run(["nm", "-D", "--defined-only", tk.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = [s for s in declared if s not in exported]
+    assert not missing, missing
+    for s in declared:
+        assert hasattr(L, s)
+
+
+@pytest.mark.parametrize("m,n", [(1, 5), (2, 9), (3, 7), (4, 40), (4, 400), (6, 80), (4, 600), (8, 12)])
+def test_packed_size(L, m, n):
+    assert tk.tk_packed_size(m, n) == oracle.packed_size(m, n)
+    assert tk.tk_packed_bytes(m, n, "bf16") == 2 * oracle.packed_size(m, n)
+
+
+def test_packed_size_overflow_and_errors(L):
+    assert L.tk_packed_size(8, 10**9) == -1
+    assert L.tk_packed_size(0, 5) == -1
+    assert L.tk_packed_size(4, -1) == -1
+    with pytest.raises(tk.TKError):
+        tk.tk_rank(4, 5, [0, 2, 1, 3])       # not sorted
+    with pytest.raises(tk.TKError):
+        tk.tk_unrank(4, 5, tk.tk_packed_size(4, 5))  # offset == N
+
+
+@pytest.mark.parametrize("m,n", [(2, 7), (3, 6), (4, 6), (6, 5), (8, 3)])
+def test_rank_unrank_bit_exact(L, m, n):
+    tuples = oracle.enumerate_tuples(m, n)
+    for off, t in enumerate(tuples):
+        assert tk.tk_rank(m, n, t) == off
+        assert tk.tk_unrank(m, n, off) == list(t)
+
+
+@pytest.mark.parametrize("m,n", [(4, 400), (4, 600), (6, 80), (4, 300), (2, 1000)])
+def test_rank_unrank_config_sizes(L, m, n):
+    N = oracle.packed_size(m, n)
+    rng = np.random.default_rng(5)
+    for off in list(rng.integers(0, N, size=200)) + [0, N - 1, N // 2]:
+        t = tk.tk_unrank(m, n, int(off))
+        assert t == list(oracle.unrank(m, n, int(off)))
+        assert tk.tk_rank(m, n, t) == off
+
+
+def test_row_align(L):
+    m, n = 4, 7
+    tuples = oracle.enumerate_tuples(m, n)
+    N = len(tuples)
+    starts = [o for o, t in enumerate(tuples) if t[-1] == t[-2]] + [N]
+    for off in range(N + 1):
+        want = min(s for s in starts if s >= off)
+        assert tk.tk_row_align(m, n, off) == want

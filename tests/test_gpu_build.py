@@ -1,0 +1,56 @@
+"""GPU parity of the packed build against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import U32, U64, UBF16, as_f64
+
+pytestmark = pytest.mark.gpu
+
+tk = pytest.importorskip("paper_2003_10482_gb300")
+
+
+def build_bound(Kabs, d, m, storage, Khat=None):
+    """|K_computed - K_exact| for an FP32 (or FP64) sum of d products of m
+    factors: gamma_{d+m} * sum_k prod_j |x|; BF16 adds the final rounding."""
+    u = U64 if storage == "f64" else U32
+    acc = 1.01 * (d + m + 2) * u * Kabs
+    if storage == "bf16":
+        return acc + UBF16 * (np.abs(Khat) + acc)
+    return acc + 1e-300
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("m,n,d", [(2, 1, 1), (2, 70, 3), (4, 1, 2), (4, 5, 3), (4, 64, 17),
+                                   (4, 65, 16), (4, 130, 5), (6, 21, 4), (8, 7, 3), (3, 40, 2)])
+def test_build_matches_oracle(m, n, d, storage):
+    X = synth.small_problem(m, n, d, salt=31 * n + d)
+    K_ref = oracle.build(X, m)
+    K_abs = oracle.build(np.abs(X), m)
+    K = tk.tk_build_packed(torch.tensor(X, device="cuda"), m, storage=storage)
+    Kh = as_f64(K)
+    err = np.abs(Kh - K_ref)
+    tol = build_bound(K_abs, d, m, storage, Kh)
+    assert np.all(err <= tol), float(np.max(err / tol))
+
+
+def test_build_ranges_are_bit_identical():
+    m, n, d = 4, 70, 6
+    X = torch.tensor(synth.small_problem(m, n, d, salt=3), device="cuda")
+    full = tk.tk_build_packed(X, m, storage="f32")
+    N = full.numel()
+    cuts = [0, 1, 999, 40000, N - 3, N]
+    parts = [tk.tk_build_packed(X, m, storage="f32", off_lo=lo, off_hi=hi) for lo, hi in zip(cuts[:-1], cuts[1:])]
+    assert torch.equal(torch.cat(parts), full)
+
+
+@pytest.mark.parametrize("feat,deg", [("poly", 2), ("poly", 3), ("exp", 1)])
+def test_build_feature_maps(feat, deg):
+    m, n, d = 4, 12, 3
+    X = 0.5 * synth.small_problem(m, n, d, salt=17)
+    code = oracle.FEAT_POLY if feat == "poly" else oracle.FEAT_EXP
+    K_ref = oracle.build(X, m, feat=code, degree=deg)
+    K = tk.tk_build_packed(torch.tensor(X, device="cuda"), m, storage="f64", feat=feat, degree=deg)
+    assert np.allclose(K.cpu().numpy(), K_ref, rtol=1e-12, atol=1e-14)
