@@ -114,7 +114,10 @@ int tk_build_packed_range(int m, int64_t n, int64_t d, const double *X, int feat
 
 /* ------------------------------------------------------------ contraction */
 
-/* Bytes of workspace tk_contract / tk_objective need for (m, n, B). */
+/* Bytes of workspace tk_contract / tk_objective need for (m, n, B).  The
+ * workspace carries a cached copy of the per-warp work plan between calls
+ * (reused while m, n, the range and the launch configuration stay the same):
+ * callers must not write into it. */
 size_t tk_contract_workspace_size(int m, int64_t n, int64_t B);
 
 /* Contractions of the symmetric tensor over its packed entries, each equal to
@@ -146,6 +149,43 @@ int tk_contract_range(int m, int64_t n, int storage_dtype, const void *K_range,
                       int64_t off_lo, int64_t off_hi, int64_t B, int vec_dtype,
                       const void *A, int r, const void *V, void *G, double *S,
                       void *work, size_t work_bytes, void *stream);
+
+/* Launch configuration of the streaming contraction kernel.  Zero fields keep
+ * the library's choice.
+ *   warps        warps per block (each warp walks its own row-aligned piece)
+ *   block_log2   log2 of the byte budget of one row block (one bulk copy)
+ *   nbuf         staging buffers per warp (nbuf-1 copies in flight), 2..8
+ *   ctas_per_sm  blocks per SM (1 or 2)
+ *   row_cost     cost of one row, in entries, when the range is cut into pieces
+ *   tri_cost     cost of entering a triangle (prefix i_1..i_{m-2}), in entries
+ *   pieces_per_warp  the range is cut into this many pieces per warp, which
+ *                warps take from a shared counter as they finish (1..16) */
+typedef struct {
+    int warps;
+    int block_log2;
+    int nbuf;
+    int ctas_per_sm;
+    int row_cost;
+    int tri_cost;
+    int pieces_per_warp;
+} tk_contract_config;
+
+/* Sets the process-wide contraction configuration (NULL restores the
+ * defaults).  Used by the autotuner; not thread-safe against concurrent
+ * contractions. */
+int tk_contract_set_config(const tk_contract_config *cfg);
+
+/* The configuration a contraction of (m, n, storage_dtype) would launch with
+ * under the current settings (dual != 0: the HVP variant). */
+int tk_contract_get_config(int m, int64_t n, int storage_dtype, int dual, tk_contract_config *out);
+
+/* Host-only: the row-aligned cut of [off_lo, off_hi) into `pieces` consecutive
+ * pieces of near-equal cost (entries + row_cost per row + tri_cost per
+ * triangle entered), as the contraction assigns them to warps.
+ * bounds_host receives pieces+1 offsets (bounds[0] = off_lo, bounds[pieces] =
+ * off_hi); every bound is a row start.  off_lo and off_hi must be row starts. */
+int tk_contract_plan(int m, int64_t n, int64_t off_lo, int64_t off_hi, int pieces, int row_cost,
+                     int tri_cost, int64_t *bounds_host);
 
 /* Reads (and clears) the device-side status word of a workspace: TK_OK, or
  * TK_ETIMEOUT if a bounded wait of an earlier call on it ran out.  Synchronises

@@ -72,6 +72,9 @@ def _declare(L):
         "tk_contract": (i32, [i32, i64, i32, P, i64, i32, P, i32, P, P, P, P, sz, P]),
         "tk_contract_range": (i32, [i32, i64, i32, P, i64, i64, i64, i32, P, i32, P, P, P, P, sz, P]),
         "tk_status_read": (i32, [P, P]),
+        "tk_contract_set_config": (i32, [P]),
+        "tk_contract_get_config": (i32, [i32, i64, i32, i32, P]),
+        "tk_contract_plan": (i32, [i32, i64, i64, i64, i32, i32, i32, P]),
         "tk_objective": (i32, [i32, i64, i32, P, i64, P, P, P, P, P, P, P, sz, P]),
     }
     for name, (res, args) in sig.items():
@@ -167,6 +170,36 @@ def workspace(m: int, n: int, B: int = 1, device=None) -> torch.Tensor:
         t = torch.zeros(need, dtype=torch.uint8, device=dev)
         _ws_cache[key] = t
     return t
+
+
+class tk_contract_config(ctypes.Structure):
+    _fields_ = [("warps", ctypes.c_int), ("block_log2", ctypes.c_int), ("nbuf", ctypes.c_int),
+                ("ctas_per_sm", ctypes.c_int), ("row_cost", ctypes.c_int), ("tri_cost", ctypes.c_int),
+                ("pieces_per_warp", ctypes.c_int)]
+
+
+def tk_contract_set_config(warps=0, block_log2=0, nbuf=0, ctas_per_sm=0, row_cost=0, tri_cost=0,
+                           pieces_per_warp=0, reset=False):
+    """Process-wide launch configuration of the contraction (0 = library choice)."""
+    if reset:
+        _check(lib().tk_contract_set_config(None))
+        return
+    c = tk_contract_config(warps, block_log2, nbuf, ctas_per_sm, row_cost, tri_cost, pieces_per_warp)
+    _check(lib().tk_contract_set_config(ctypes.byref(c)))
+
+
+def tk_contract_plan(m: int, n: int, off_lo: int, off_hi: int, pieces: int, row_cost: int = 48,
+                     tri_cost: int = 192) -> list[int]:
+    """Row-aligned cut of [off_lo, off_hi) into `pieces` near-equal-cost pieces (host only)."""
+    out = (ctypes.c_int64 * (pieces + 1))()
+    _check(lib().tk_contract_plan(m, n, off_lo, off_hi, pieces, row_cost, tri_cost, out))
+    return list(out)
+
+
+def tk_contract_get_config(m: int, n: int, storage="f32", dual: bool = False) -> dict:
+    c = tk_contract_config()
+    _check(lib().tk_contract_get_config(m, n, dtype_code(storage), int(dual), ctypes.byref(c)))
+    return {f: getattr(c, f) for f, _ in c._fields_}
 
 
 def tk_status_read(work: torch.Tensor, stream=None) -> int:

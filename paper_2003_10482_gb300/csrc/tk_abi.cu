@@ -3,6 +3,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "tk_internal.h"
 
@@ -132,8 +133,7 @@ size_t tk_contract_workspace_size(int m, int64_t n, int64_t B) {
   if (check_order_points(m, n) != TK_OK) return 0;
   DevInfo di;
   if (dev_info(&di) != TK_OK) return 0;
-  // up to 2 blocks per SM
-  return sizeof(WsHeader) + contract_part_bytes((int)n, 2 * di.sms);
+  return contract_workspace_bytes((int)n, di.sms);
 }
 
 static int contract_impl(int m, int64_t n, int storage, const void *K, int64_t off_lo, int64_t off_hi,
@@ -157,7 +157,7 @@ static int contract_impl(int m, int64_t n, int storage, const void *K, int64_t o
   DevInfo di;
   rc = dev_info(&di);
   if (rc != TK_OK) return rc;
-  const size_t need = sizeof(WsHeader) + contract_part_bytes((int)n, 2 * di.sms);
+  const size_t need = contract_workspace_bytes((int)n, di.sms);
   if (work_bytes < need) return fail(TK_ENOMEM, "workspace %zu < %zu bytes", work_bytes, need);
 
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -175,10 +175,11 @@ static int contract_impl(int m, int64_t n, int storage, const void *K, int64_t o
     a.vec_dtype = vec_dtype;
     a.alpha = reinterpret_cast<const unsigned char *>(A) + b * n * vs;
     a.v = (r == m - 2) ? reinterpret_cast<const unsigned char *>(V) + b * n * vs : nullptr;
-    a.part = reinterpret_cast<double *>(wsb + sizeof(WsHeader));
+    a.work = wsb;
     a.status = reinterpret_cast<int *>(wsb);
     int grid = 0;
-    rc = contract_pass(a, &grid, st);
+    const double *part = nullptr;
+    rc = contract_pass(a, &grid, &part, st);
     if (rc != TK_OK) return rc;
     FinalizeArgs f;
     memset(&f, 0, sizeof(f));
@@ -186,7 +187,7 @@ static int contract_impl(int m, int64_t n, int storage, const void *K, int64_t o
     f.m = m;
     f.n = (int)n;
     f.grid = grid;
-    f.part = a.part;
+    f.part = part;
     f.out_dtype = vec_dtype;
     f.G = reinterpret_cast<unsigned char *>(G) + b * n * vs;
     f.S = (S && r == m - 1) ? S + b : nullptr;
@@ -208,6 +209,45 @@ int tk_contract_range(int m, int64_t n, int storage, const void *K_range, int64_
                       void *work, size_t work_bytes, void *stream) {
   return contract_impl(m, n, storage, K_range, off_lo, off_hi, B, vec_dtype, A, r, V, G, S, work, work_bytes,
                        stream);
+}
+
+int tk_contract_set_config(const tk_contract_config *cfg) {
+  if (!cfg) {
+    g_contract_cfg = tk_contract_config{0, 0, 0, 0, 0, 0, 0};
+    return TK_OK;
+  }
+  if (cfg->warps < 0 || cfg->warps > 16 || (cfg->block_log2 != 0 && (cfg->block_log2 < 9 || cfg->block_log2 > 15)) ||
+      (cfg->nbuf != 0 && (cfg->nbuf < 2 || cfg->nbuf > 8)) || cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 2 ||
+      cfg->row_cost < 0 || cfg->tri_cost < 0 || cfg->pieces_per_warp < 0 || cfg->pieces_per_warp > 16)
+    return fail(TK_EINVAL, "contract config out of range");
+  g_contract_cfg = *cfg;
+  return TK_OK;
+}
+
+int tk_contract_plan(int m, int64_t n, int64_t off_lo, int64_t off_hi, int pieces, int row_cost, int tri_cost,
+                     int64_t *bounds) {
+  if (!bounds) return fail(TK_EINVAL, "NULL output");
+  int rc = check_order_points(m, n);
+  if (rc != TK_OK) return rc;
+  if (pieces < 1 || row_cost < 0 || tri_cost < 0) return fail(TK_EINVAL, "bad pieces or costs");
+  const int64_t N = multiset(n, m);
+  if (off_lo < 0 || off_hi > N || off_lo > off_hi) return fail(TK_EINVAL, "range outside [0, N]");
+  if (!is_row_start(m, n, off_lo, N) || !is_row_start(m, n, off_hi, N))
+    return fail(TK_EINVAL, "range ends must be row starts (tk_row_align)");
+  std::vector<WarpPlan> v(pieces);
+  build_plan(m, (int)n, off_lo, off_hi, pieces, row_cost, tri_cost, v.data());
+  for (int i = 0; i < pieces; ++i) bounds[i] = v[i].start;
+  bounds[pieces] = v[pieces - 1].end;
+  return TK_OK;
+}
+
+int tk_contract_get_config(int m, int64_t n, int storage, int dual, tk_contract_config *out) {
+  if (!out) return fail(TK_EINVAL, "NULL output");
+  int rc = check_order_points(m, n);
+  if (rc != TK_OK) return rc;
+  if (storage < TK_F64 || storage > TK_BF16) return fail(TK_EINVAL, "bad storage dtype %d", storage);
+  int grid = 0;
+  return contract_resolve(m, (int)n, storage, dual != 0, out, &grid);
 }
 
 int tk_status_read(void *work, void *stream) {
@@ -238,7 +278,7 @@ int tk_objective(int m, int64_t n, int storage, const void *K, int64_t B, const 
   DevInfo di;
   rc = dev_info(&di);
   if (rc != TK_OK) return rc;
-  const size_t need = sizeof(WsHeader) + contract_part_bytes((int)n, 2 * di.sms);
+  const size_t need = contract_workspace_bytes((int)n, di.sms);
   if (work_bytes < need) return fail(TK_ENOMEM, "workspace %zu < %zu bytes", work_bytes, need);
   const int64_t N = multiset(n, m);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -254,10 +294,11 @@ int tk_objective(int m, int64_t n, int storage, const void *K, int64_t B, const 
     a.off_hi = N;
     a.vec_dtype = TK_F64;
     a.alpha = A + b * n;
-    a.part = reinterpret_cast<double *>(wsb + sizeof(WsHeader));
+    a.work = wsb;
     a.status = reinterpret_cast<int *>(wsb);
     int grid = 0;
-    rc = contract_pass(a, &grid, st);
+    const double *part = nullptr;
+    rc = contract_pass(a, &grid, &part, st);
     if (rc != TK_OK) return rc;
     FinalizeArgs f;
     memset(&f, 0, sizeof(f));
@@ -265,7 +306,7 @@ int tk_objective(int m, int64_t n, int storage, const void *K, int64_t B, const 
     f.m = m;
     f.n = (int)n;
     f.grid = grid;
-    f.part = a.part;
+    f.part = part;
     f.alpha = A + b * n;
     f.y = y;
     f.lambda = lambda + b;

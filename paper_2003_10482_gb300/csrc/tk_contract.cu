@@ -1,6 +1,11 @@
 // Host side of the packed contraction: launch configuration of the streaming
 // kernel (tk_contract_impl.cuh) and the fixed-order FP64 reduction of the
 // per-block partial sums.
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
 #include "tk_contract_impl.cuh"
 
 namespace tk {
@@ -75,72 +80,240 @@ static int pick_nc(int n) {
   return -1;
 }
 
-static int max_threads_for(int storage, bool dual, int nc) {
-  return max_threads_est(storage == TK_F64 ? 8 : 4, dual, nc);
-}
 
+tk_contract_config g_contract_cfg = {0, 0, 0, 0, 0, 0, 0};
+
+static const int kMaxWarps = 16;
+
+static const int kMaxPiecesPerWarp = 16;
+size_t contract_plan_bytes(int sms) { return (size_t)kMaxPiecesPerWarp * 2 * sms * kMaxWarps * sizeof(WarpPlan); }
 size_t contract_part_bytes(int n, int grid) { return (size_t)grid * 2 * (size_t)(n + 2) * sizeof(double); }
-
-int contract_default_grid() {
-  DevInfo di;
-  if (dev_info(&di) != TK_OK) return -1;
-  return di.sms;
+size_t contract_workspace_bytes(int n, int sms) {
+  return sizeof(WsHeader) + contract_plan_bytes(sms) + contract_part_bytes(n, 2 * sms);
 }
 
-int contract_pass(const ContractArgs &a, int *grid_out, cudaStream_t st) {
+// ------------------------------------------------------------------ plan
+// Walk rows from `lo` in layout order.  Row c of triangle Q holds n - c
+// entries; a triangle's remaining rows c..n-1 hold (n-c)(n-c+1)/2 entries.
+struct RowCursor {
+  int m, n;
+  int32_t t[kMaxOrder];  // Q in t[0..m-3], c in t[m-2]
+  int64_t pos;
+  bool next_triangle() {
+    if (m <= 2) return false;
+    if (!next_sorted(m - 2, n, t)) return false;
+    t[m - 2] = t[m - 3];
+    return true;
+  }
+};
+
+void build_plan(int m, int n, int64_t lo, int64_t hi, int pieces, int64_t row_cost, int64_t tri_cost,
+                WarpPlan *out) {
+  RowCursor cu;
+  cu.m = m;
+  cu.n = n;
+  for (int j = 0; j < kMaxOrder; ++j) cu.t[j] = 0;
+  if (lo < hi) unrank(m, n, lo, cu.t);
+  cu.pos = lo;
+  // pass 1: total cost
+  int64_t total = 0;
+  {
+    RowCursor w = cu;
+    while (w.pos < hi) {
+      total += tri_cost;
+      const int64_t R = n - w.t[m - 2];
+      const int64_t E = R * (R + 1) / 2;
+      if (w.pos + E <= hi) {
+        total += E + row_cost * R;
+        w.pos += E;
+        if (w.pos < hi && !w.next_triangle()) break;
+      } else {
+        while (w.pos < hi) {
+          total += (n - w.t[m - 2]) + row_cost;
+          w.pos += n - w.t[m - 2];
+          w.t[m - 2] += 1;
+        }
+      }
+    }
+  }
+  // pass 2: the first row start whose preceding cost reaches w * total / pieces
+  int wi = 1;
+  auto target = [&](int w) { return (int64_t)((__int128)total * w / pieces); };
+  auto emit = [&](const RowCursor &at) {
+    out[wi - 1].end = at.pos;
+    out[wi].start = at.pos;
+    for (int j = 0; j < kMaxOrder; ++j) out[wi].t[j] = at.t[j];
+    ++wi;
+  };
+  out[0].start = lo;
+  for (int j = 0; j < kMaxOrder; ++j) out[0].t[j] = cu.t[j];
+  int64_t cum = 0;
+  RowCursor w = cu;
+  while (w.pos < hi && wi < pieces) {
+    cum += tri_cost;
+    const int64_t R = n - w.t[m - 2];
+    const int64_t E = R * (R + 1) / 2;
+    const bool whole = w.pos + E <= hi;
+    if (whole && cum + E + row_cost * R < target(wi)) {
+      cum += E + row_cost * R;
+      w.pos += E;
+      if (w.pos < hi && !w.next_triangle()) break;
+      continue;
+    }
+    // a cut falls inside this triangle (or the range ends in it): row by row
+    while (w.pos < hi && w.t[m - 2] < n) {
+      while (wi < pieces && cum >= target(wi)) emit(w);
+      cum += (n - w.t[m - 2]) + row_cost;
+      w.pos += n - w.t[m - 2];
+      w.t[m - 2] += 1;
+    }
+    if (w.pos < hi && !w.next_triangle()) break;
+  }
+  RowCursor endc = w;
+  endc.pos = hi;
+  while (wi < pieces) emit(endc);
+  out[pieces - 1].end = hi;
+}
+
+struct PlanKey {
+  int m, n;
+  int64_t lo, hi;
+  int pieces, rc, tc;
+  bool operator<(const PlanKey &o) const {
+    return std::tie(m, n, lo, hi, pieces, rc, tc) < std::tie(o.m, o.n, o.lo, o.hi, o.pieces, o.rc, o.tc);
+  }
+  bool operator==(const PlanKey &o) const { return !(*this < o) && !(o < *this); }
+};
+
+static std::mutex g_plan_mu;
+static std::map<PlanKey, std::vector<WarpPlan>> g_plans;
+static std::map<std::pair<int, const void *>, PlanKey> g_uploaded;
+
+// Make sure the plan for `key` sits in the workspace's plan region.
+static int ensure_plan(const PlanKey &key, void *plan_region, cudaStream_t st) {
+  int dev = 0;
+  TK_CUDA_CHECK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  auto up = g_uploaded.find({dev, plan_region});
+  if (up != g_uploaded.end() && up->second == key) return TK_OK;
+  auto it = g_plans.find(key);
+  if (it == g_plans.end()) {
+    if (g_plans.size() > 32) g_plans.clear();
+    std::vector<WarpPlan> v(key.pieces);
+    build_plan(key.m, key.n, key.lo, key.hi, key.pieces, key.rc, key.tc, v.data());
+    it = g_plans.emplace(key, std::move(v)).first;
+  }
+  TK_CUDA_CHECK(cudaMemcpyAsync(plan_region, it->second.data(), it->second.size() * sizeof(WarpPlan),
+                                cudaMemcpyHostToDevice, st));
+  g_uploaded[{dev, plan_region}] = key;
+  return TK_OK;
+}
+
+// ------------------------------------------------------------------ launch config
+struct Resolved {
+  int nc, warps, nbuf, buf_bytes, cap, vec_bytes, warp_bytes, grid, cps, row_cost, tri_cost, block_log2, ppw;
+  size_t smem;
+};
+
+static int resolve(int m, int n, int storage, bool dual, Resolved *r) {
   DevInfo di;
   int rc = dev_info(&di);
   if (rc != TK_OK) return rc;
-  const bool dual = a.v != nullptr;
-  const int es = dtype_size(a.storage);
-  const int cts = a.storage == TK_F64 ? 8 : 4;
-  const int nc = pick_nc(a.n);
-  if (nc < 0) return fail(TK_EUNSUPPORTED, "contract: n=%d exceeds %d", a.n, TK_MAX_POINTS);
+  (void)m;
+  const int es = dtype_size(storage);
+  const int cts = storage == TK_F64 ? 8 : 4;
+  r->nc = pick_nc(n);
+  if (r->nc < 0) return fail(TK_EUNSUPPORTED, "contract: n=%d exceeds %d", n, TK_MAX_POINTS);
+  const tk_contract_config &o = g_contract_cfg;
+  int bl = o.block_log2 > 0 ? o.block_log2 : 12;
+  if (bl < 9 || bl > 15) return fail(TK_EINVAL, "block_log2 outside [9, 15]");
+  while ((1 << bl) < n * es) ++bl;  // one full row must fit a block
+  r->block_log2 = bl;
+  r->cap = (1 << bl) / es;
+  r->buf_bytes = (((1 << bl) + 32) + 127) & ~127;
+  r->nbuf = o.nbuf > 0 ? o.nbuf : 2;
+  if (r->nbuf < 2 || r->nbuf > 8) return fail(TK_EINVAL, "nbuf outside [2, 8]");
+  const int fixed = cts == 8 ? (dual ? warp_fixed_bytes<double, true>() : warp_fixed_bytes<double, false>())
+                              : (dual ? warp_fixed_bytes<float, true>() : warp_fixed_bytes<float, false>());
+  const int gbytes = ((dual ? 2 : 1) * n * cts + 127) & ~127;
+  r->vec_bytes = ((dual ? 2 : 1) * n * cts + 127) & ~127;
+  r->warp_bytes = fixed + gbytes + r->nbuf * r->buf_bytes;
+  r->warp_bytes = (r->warp_bytes + 127) & ~127;
+  r->cps = o.ctas_per_sm > 0 ? o.ctas_per_sm : 1;
+  if (r->cps > 2) return fail(TK_EINVAL, "ctas_per_sm must be 1 or 2");
+  const int smem_budget = (di.smem_optin - 1024) / r->cps;
+  const int warps_fit = (smem_budget - r->vec_bytes) / r->warp_bytes;
+  int warps = o.warps > 0 ? o.warps : kMaxWarps;
+  warps = std::min(warps, max_threads_est(cts, dual, r->nc) / 32);
+  warps = std::min(warps, warps_fit);
+  if (warps < 1) return fail(TK_EUNSUPPORTED, "contract: shared memory too small for one warp");
+  r->warps = warps;
+  r->grid = di.sms * r->cps;
+  r->smem = (size_t)r->vec_bytes + (size_t)warps * r->warp_bytes;
+  r->row_cost = o.row_cost > 0 ? o.row_cost : 1024;
+  r->tri_cost = o.tri_cost > 0 ? o.tri_cost : 4 * r->row_cost;
+  r->ppw = o.pieces_per_warp > 0 ? o.pieces_per_warp : 16;
+  if (r->ppw > kMaxPiecesPerWarp) return fail(TK_EINVAL, "pieces_per_warp above %d", kMaxPiecesPerWarp);
+  return TK_OK;
+}
 
+int contract_resolve(int m, int n, int storage, bool dual, tk_contract_config *out, int *grid) {
+  Resolved r;
+  int rc = resolve(m, n, storage, dual, &r);
+  if (rc != TK_OK) return rc;
+  out->warps = r.warps;
+  out->block_log2 = r.block_log2;
+  out->nbuf = r.nbuf;
+  out->ctas_per_sm = r.cps;
+  out->row_cost = r.row_cost;
+  out->tri_cost = r.tri_cost;
+  out->pieces_per_warp = r.ppw;
+  if (grid) *grid = r.grid;
+  return TK_OK;
+}
+
+int contract_pass(const ContractArgs &a, int *grid_out, const double **part_out, cudaStream_t st) {
+  const bool dual = a.v != nullptr;
+  Resolved r;
+  int rc = resolve(a.m, a.n, a.storage, dual, &r);
+  if (rc != TK_OK) return rc;
+  DevInfo di;
+  dev_info(&di);
+  unsigned char *ws = reinterpret_cast<unsigned char *>(a.work);
+  WarpPlan *plan = reinterpret_cast<WarpPlan *>(ws + sizeof(WsHeader));
+  double *part = reinterpret_cast<double *>(ws + sizeof(WsHeader) + contract_plan_bytes(di.sms));
+  const int pieces = r.ppw * r.grid * r.warps;
+  PlanKey key{a.m, a.n, a.off_lo, a.off_hi, pieces, r.row_cost, r.tri_cost};
+  rc = ensure_plan(key, plan, st);
+  if (rc != TK_OK) return rc;
+  WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
+  TK_CUDA_CHECK(cudaMemsetAsync(&hdr->ticket, 0, sizeof(hdr->ticket), st));
   KParams kp;
   kp.m = a.m;
   kp.n = a.n;
   kp.K = reinterpret_cast<const unsigned char *>(a.K);
   kp.off_lo = a.off_lo;
   kp.off_hi = a.off_hi;
-  kp.bytes = (a.off_hi - a.off_lo) * es;
+  kp.bytes = (a.off_hi - a.off_lo) * dtype_size(a.storage);
   kp.alpha = a.alpha;
   kp.v = a.v;
   kp.vec_dtype = a.vec_dtype;
-  kp.part = a.part;
+  kp.part = part;
   kp.status = a.status;
-
-  // ring: a batch of kRB rows (<= kRB * n entries) must fit in NS-1 slots
-  kp.slot_log2 = a.slot_log2 > 0 ? a.slot_log2 : 11;
-  const int64_t slot = 1ll << kp.slot_log2;
-  const int64_t batch_bytes = (int64_t)kRB * a.n * es + 32;
-  int need = (int)((batch_bytes + slot - 1) / slot) + 2;
-  int ns_log2 = 2;
-  while ((1 << ns_log2) < need) ++ns_log2;
-  if (a.ns_log2 > 0) {
-    if (a.ns_log2 < ns_log2) return fail(TK_EINVAL, "contract: ring of 2^%d slots too small", a.ns_log2);
-    ns_log2 = a.ns_log2;
-  }
-  if (ns_log2 > 4) return fail(TK_EUNSUPPORTED, "contract: ring needs more than 16 slots");
-  kp.ns_log2 = ns_log2;
-  const int64_t ring = slot << ns_log2;
-  kp.vec_bytes = (int)(((int64_t)(dual ? 2 : 1) * a.n * cts + 127) & ~127ll);
-  kp.warp_bytes = (int)((128 + ring + (int64_t)(dual ? 2 : 1) * a.n * cts + 127) & ~127ll);
-  const int smem_budget = di.smem_optin - 1024;  // static shared + slack
-  int warps_fit = (smem_budget - kp.vec_bytes) / kp.warp_bytes;
-  int warps = a.warps > 0 ? a.warps : 16;
-  warps = std::min(warps, max_threads_for(a.storage, dual, nc) / 32);
-  warps = std::min(warps, warps_fit);
-  if (warps < 1) return fail(TK_EUNSUPPORTED, "contract: shared memory too small for one warp");
-  kp.warps = warps;
-  const int cps = a.ctas_per_sm > 0 ? a.ctas_per_sm : 1;
-  const int grid = di.sms * cps;
-  const size_t smem = (size_t)kp.vec_bytes + (size_t)warps * kp.warp_bytes;
-  if (grid_out) *grid_out = grid;
-
-  if (a.storage == TK_F64) return contract_launch_f64(kp, dual, nc, grid, warps * 32, smem, st);
-  if (a.storage == TK_F32) return contract_launch_f32(kp, dual, nc, grid, warps * 32, smem, st);
-  return contract_launch_bf16(kp, dual, nc, grid, warps * 32, smem, st);
+  kp.plan = plan;
+  kp.pieces = pieces;
+  kp.ticket = &hdr->ticket;
+  kp.warps = r.warps;
+  kp.nbuf = r.nbuf;
+  kp.buf_bytes = r.buf_bytes;
+  kp.cap = r.cap;
+  kp.vec_bytes = r.vec_bytes;
+  kp.warp_bytes = r.warp_bytes;
+  if (grid_out) *grid_out = r.grid;
+  if (part_out) *part_out = part;
+  if (a.storage == TK_F64) return contract_launch_f64(kp, dual, r.nc, r.grid, r.warps * 32, r.smem, st);
+  if (a.storage == TK_F32) return contract_launch_f32(kp, dual, r.nc, r.grid, r.warps * 32, r.smem, st);
+  return contract_launch_bf16(kp, dual, r.nc, r.grid, r.warps * 32, r.smem, st);
 }
 
 int contract_finalize(const FinalizeArgs &f, cudaStream_t st) {

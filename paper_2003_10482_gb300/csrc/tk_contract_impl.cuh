@@ -21,20 +21,23 @@
 // numbers) gives d/deps K[(a+eps v)^{m-1}] = (m-1) K[a^{m-2}, v] in the same
 // pass.
 //
-// GB300 mapping.  Every warp owns a contiguous, row-aligned range of the packed
-// array and streams it through its own shared-memory ring with
-// cp.async.bulk (TMA bulk copies, mbarrier completion), so each SM keeps
-// ~100 KB of HBM reads in flight with a handful of instructions.  Within a
-// row, lane j owns the columns d = n-1-(32k+j): the last index is counted
-// from the end of the row, so every row of a triangle starts at chunk 0.  The
-// per-entry scatter to g_d then accumulates in registers (acc[k]) with no
-// atomics, the row dot r_c is a per-lane partial sum, and RB = 4 rows are
-// processed together so that their dots are reduce-scattered across the
-// warp with 6 shuffles.  Per-warp partial g lives in shared memory; blocks
-// write FP64 partials that a second kernel sums in a fixed order.
+// GB300 mapping.  The host cuts the packed range into one row-aligned piece
+// per warp, balanced by cost (entries + a weight per row + a weight per
+// triangle, tk_contract_plan).  Each warp walks its rows in blocks of at most
+// 16 consecutive rows of one triangle whose entries fit a byte budget; every
+// block is fetched by one cp.async.bulk copy (TMA bulk engine, mbarrier
+// completion) into one of NBUF linear shared-memory buffers, so NBUF-1 blocks
+// are always in flight while the warp computes on the current one.  Within a
+// row, lane j owns the columns d = n-1-(32k+j): the last index is counted from
+// the end of the row, so every row of a triangle starts at chunk 0 and the
+// per-entry scatter to g_d accumulates in registers (acc[k]) with no atomics.
+// The per-lane partial row dots of a block go to a padded shared-memory tile
+// and are summed two lanes per row; the per-row epilogue runs on 16 lanes in
+// parallel.  Per-warp partial g lives in shared memory; blocks write FP64
+// partials that a second kernel sums in a fixed order.
+#pragma once
 #include <cuda_bf16.h>
 
-#pragma once
 #include <algorithm>
 
 #include "tk_internal.h"
@@ -154,38 +157,36 @@ __device__ __forceinline__ float ld_ring<__nv_bfloat16, float>(const unsigned ch
   return __uint_as_float(h << 16);
 }
 
+template <typename ST, typename CT>
+__device__ __forceinline__ CT ld_elem(const ST *p);
+template <>
+__device__ __forceinline__ float ld_elem<float, float>(const float *p) {
+  return *p;
+}
+template <>
+__device__ __forceinline__ double ld_elem<double, double>(const double *p) {
+  return *p;
+}
+template <>
+__device__ __forceinline__ float ld_elem<__nv_bfloat16, float>(const __nv_bfloat16 *p) {
+  const uint32_t h = *reinterpret_cast<const unsigned short *>(p);
+  return __uint_as_float(h << 16);
+}
+
 template <typename CT>
 __device__ __forceinline__ CT ld_vec(const void *p, int dt, int i) {
   return dt == TK_F64 ? (CT) reinterpret_cast<const double *>(p)[i]
                       : (CT) reinterpret_cast<const float *>(p)[i];
 }
 
-// Warp-cooperative unrank (see tk_core.h): each position is located by a
-// 32-way search, two rounds for n <= 1024.
-static __device__ void warp_unrank(int m, int64_t n, int64_t off, int32_t *t, int lane) {
-  int64_t lo = 0;
-  for (int j = 0; j < m; ++j) {
-    int r = m - 1 - j;
-    int64_t a = lo, b = n - 1;
-    while (a < b) {
-      int64_t step = (b - a + 31) >> 5;
-      int64_t cand = a + (int64_t)(lane + 1) * step;
-      bool ok = (cand <= b) && (before(n, r, lo, cand) <= off);
-      unsigned msk = __ballot_sync(0xffffffffu, ok);
-      if (msk == 0) {
-        b = a + step - 1;
-      } else {
-        int hl = 31 - __clz(msk);
-        int64_t ch = a + (int64_t)(hl + 1) * step;
-        a = ch;
-        b = min(b, ch + step - 1);
-      }
-    }
-    off -= before(n, r, lo, a);
-    t[j] = (int32_t)a;
-    lo = a;
-  }
-}
+
+constexpr int kRB = 16;  // rows per block (upper bound)
+
+// Dot tile: lane l's partial dot of row r sits at dsm_index(l, r); a lane's
+// four dots of a quad are contiguous (one 128-bit store), and the 16-lane
+// reduction reads it without bank conflicts.
+__device__ __forceinline__ int dsm_index(int l, int r) { return l * 20 + r + 16 * (l >> 4); }
+constexpr int kDsmLen = 32 * 20 + 16;
 
 struct KParams {
   int m, n;
@@ -197,13 +198,16 @@ struct KParams {
   int vec_dtype;
   double *part;
   int *status;
+  const WarpPlan *plan;      // cost-balanced pieces of the range
+  int pieces;
+  unsigned long long *ticket;  // next piece to hand out (zeroed before the launch)
   int warps;
-  int slot_log2, ns_log2;
-  int vec_bytes;   // bytes of the staged alpha (and v) region, 128-aligned
-  int warp_bytes;  // bytes of one warp's region
+  int nbuf;         // linear staging buffers per warp
+  int buf_bytes;    // bytes of one buffer (block budget + alignment slack)
+  int cap;          // block budget in entries
+  int vec_bytes;    // bytes of the staged alpha (and v) region, 128-aligned
+  int warp_bytes;   // bytes of one warp's region
 };
-
-constexpr int kRB = 4;  // rows per batch
 
 // Threads per block the register budget allows: a base of ~64 registers plus
 // the per-lane column state (acc[] and alpha[], doubled for dual numbers and
@@ -214,6 +218,61 @@ __host__ __device__ constexpr int max_threads_est(int ct_bytes, bool dual, int n
 template <typename CT, bool D, int NC>
 constexpr int max_threads() {
   return max_threads_est((int)sizeof(CT), D, NC);
+}
+
+// Per-warp shared-memory header: NBUF mbarriers and the row count and piece
+// of each issued block.
+struct WarpHdr {
+  uint64_t bar[8];
+  int nb[8];
+  int piece[8];
+  int pad[8];
+};
+static_assert(sizeof(WarpHdr) == 160, "warp header");
+
+// Per-row data of the current block, written by lane i for row i and read
+// back by the whole warp with one broadcast load.
+template <typename CT>
+struct __align__(16) RowInfo {
+  CT cf_v, cf_d;  // coefficient of the per-entry scatter (value, derivative)
+  int rowend;     // index of the row's last entry in the block buffer
+  int sl;         // entries after the head
+};
+
+template <typename CT, bool D>
+__host__ __device__ constexpr int warp_fixed_bytes() {
+  // header, row info, dot tile(s); 128-byte aligned
+  return ((160 + kRB * (int)sizeof(RowInfo<CT>) + (D ? 2 : 1) * kDsmLen * (int)sizeof(CT)) + 127) & ~127;
+}
+
+// rows of the block that starts at row c (position pos) of its triangle:
+// at most kRB, within the triangle, within `cap` entries (rows shrink by one
+// entry each, so cap / L0 rows always fit), not past `end`
+__device__ __forceinline__ int block_rows(int n, int c, int64_t pos, int64_t end, int cap) {
+  const int L0 = n - c;
+  int r = min(min(kRB, L0), max(1, (int)__fdividef((float)cap, (float)L0)));
+  while (r < min(kRB, L0) && (r + 1) * L0 - ((r + 1) * r) / 2 <= cap) ++r;
+  while (r > 1 && pos + (int64_t)(r * L0 - (r * (r - 1)) / 2) > end) --r;
+  return r;
+}
+
+// One 32-column chunk of four consecutive rows: lane j takes, in each row i,
+// the entry of column d = n-1-(32K+j), adds it into g_d's accumulator and into
+// row i's dot.  MASK: the chunk may run past the end of a row.
+template <int K, bool MASK, int NC, typename ST, typename CT, bool D>
+__device__ __forceinline__ void quad_chunk(Nm<CT, D> (&acc)[NC], Nm<CT, D> (&dot)[4], const Nm<CT, D> (&ar)[NC],
+                                           const ST *const (&prow)[4], const int (&sl)[4], int lane,
+                                           const Nm<CT, D> (&cf)[4]) {
+  if constexpr (K < NC) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (!MASK || 32 * K + lane < sl[i]) {
+        const CT x = ld_elem<ST, CT>(prow[i] - 32 * K);
+        fma_acc(acc[K], x, cf[i]);
+        fma_acc(dot[i], x, ar[K]);
+      }
+    }
+  }
 }
 
 template <typename ST, typename CT, bool D, int NC>
@@ -229,13 +288,15 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
   CT *a_s = reinterpret_cast<CT *>(smem);
   CT *v_s = a_s + n;
   unsigned char *wb = smem + p.vec_bytes + (size_t)wid * p.warp_bytes;
-  uint64_t *bar = reinterpret_cast<uint64_t *>(wb);
-  unsigned char *ring = wb + 128;
-  const uint32_t SLOT = 1u << p.slot_log2;
-  const uint32_t NS = 1u << p.ns_log2;
-  const uint32_t RING = SLOT * NS;
-  CT *g_v = reinterpret_cast<CT *>(ring + RING);
+  WarpHdr *hdr = reinterpret_cast<WarpHdr *>(wb);
+  RowInfo<CT> *rinfo = reinterpret_cast<RowInfo<CT> *>(wb + 160);
+  CT *dsm_v = reinterpret_cast<CT *>(wb + 160 + kRB * sizeof(RowInfo<CT>));
+  CT *dsm_d = dsm_v + kDsmLen;
+  CT *g_v = reinterpret_cast<CT *>(wb + warp_fixed_bytes<CT, D>());
   CT *g_d = g_v + n;
+  const int gbytes = (int)((((D ? 2 : 1) * n * (int)sizeof(CT)) + 127) & ~127);
+  unsigned char *bufs = wb + warp_fixed_bytes<CT, D>() + gbytes;
+  const int NB = p.nbuf;
 
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     a_s[i] = ld_vec<CT>(p.alpha, p.vec_dtype, i);
@@ -246,96 +307,79 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
     if (D) g_d[i] = CT(0);
   }
   if (lane == 0) {
-    for (uint32_t s = 0; s < NS; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < NB; ++s) mbar_init(&hdr->bar[s], 1);
     fence_barrier_init();
   }
   __syncthreads();
 
   auto alpha_at = [&](int i) -> N { return mk<CT, D>(a_s[i], D ? v_s[i] : CT(0)); };
 
-  // ------------------------------------------------------------ warp range
-  const int64_t W = (int64_t)gridDim.x * p.warps;
-  const int64_t w = (int64_t)blockIdx.x * p.warps + wid;
-  const int64_t total = p.off_hi - p.off_lo;
-  int64_t o0 = p.off_lo + (w * total) / W;
-  int64_t o1 = p.off_lo + ((w + 1) * total) / W;
-
-  int32_t Q[kMaxOrder];
-  int32_t tt[kMaxOrder];
-  int c = 0;
-  int64_t p_row = p.off_hi, p_end = p.off_hi;
-  bool have = false;
-  if (o0 < p.off_hi) {
-    warp_unrank(m, n, o0, tt, lane);
-    c = tt[m - 2];
-    int dl = tt[m - 1];
-    p_row = (dl == c) ? o0 : o0 + (n - dl);
-    if (dl != c) c += 1;
-    for (int j = 0; j < m - 2; ++j) Q[j] = tt[j];
-    if (c == n) {
-      // the next row starts a new triangle
-      if (m > 2 && next_sorted(m - 2, n, Q)) c = Q[m - 3];
-      else p_row = p.off_hi;
-    }
-    if (o1 < p.off_hi) {
-      warp_unrank(m, n, o1, tt, lane);
-      int c1 = tt[m - 2], d1 = tt[m - 1];
-      p_end = (d1 == c1) ? o1 : o1 + (n - d1);
-    }
-    have = p_row < p_end;
+  // ------------------------------------------------------------ pieces
+  // Warps take cost-balanced pieces of the range from a shared ticket: the
+  // copy side of a warp takes the next piece when it has issued every block
+  // of the current one, and tags each block with its piece so that the
+  // compute side switches in step.
+  auto grab = [&]() -> int {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(p.ticket, 1ull);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    return t < (unsigned long long)p.pieces ? (int)t : -1;
+  };
+  int32_t Q[kMaxOrder], Qp[kMaxOrder];
+  int c = 0, cp = 0;
+  int64_t pos = 0, end = 0, posp = 0, endp = 0;
+  int piece_p = grab();
+  if (piece_p >= 0) {
+    const WarpPlan &pl = p.plan[piece_p];
+    for (int j = 0; j < kMaxOrder; ++j) Qp[j] = pl.t[j];
+    cp = pl.t[m - 2];
+    posp = pl.start;
+    endp = pl.end;
   }
+  bool prod_done = piece_p < 0;
+  int piece_c = -1;
 
-  // ------------------------------------------------------------ ring
-  const int64_t rel0 = (p_row - p.off_lo) * ES;
-  const int64_t rel1 = (p_end - p.off_lo) * ES;
-  const int64_t sbase = rel0 & ~int64_t(15);
   const int64_t tail_lo = p.bytes & ~int64_t(15);
-  const int64_t bulk_lim = min((rel1 + 15) & ~int64_t(15), tail_lo);
-  const uint32_t emask = RING / ES - 1;
-  const uint32_t ebase = (uint32_t)(p.off_lo + sbase / ES);
-  int64_t s_issued = 0, s_ready = 0;
+  int64_t j_issue = 0, j_cons = 0;
   bool failed = false;
 
-  auto issue = [&](int64_t s) {
-    const int64_t lo = sbase + (s << p.slot_log2);
-    if (lo >= bulk_lim) return;
-    const int64_t rem = bulk_lim - lo;
-    const uint32_t sz = rem < (int64_t)SLOT ? (uint32_t)rem : SLOT;
+  // issue the bulk copy of the next block at the copy cursor
+  auto issue_next = [&]() {
+    while (!prod_done && posp >= endp) {
+      piece_p = grab();
+      if (piece_p < 0) {
+        prod_done = true;
+        return;
+      }
+      const WarpPlan &pl = p.plan[piece_p];
+      for (int j = 0; j < kMaxOrder; ++j) Qp[j] = pl.t[j];
+      cp = pl.t[m - 2];
+      posp = pl.start;
+      endp = pl.end;
+    }
+    if (prod_done) return;
+    const int nb = block_rows(n, cp, posp, endp, p.cap);
+    const int L0 = n - cp;
+    const int64_t pend = posp + (int64_t)(nb * L0 - (nb * (nb - 1)) / 2);
+    const int bi = (int)(j_issue % NB);
+    const int64_t b0 = ((posp - p.off_lo) * ES) & ~int64_t(15);
+    const int64_t b1 = min((((pend - p.off_lo) * ES) + 15) & ~int64_t(15), tail_lo);
     if (lane == 0) {
-      uint64_t *b = &bar[s & (NS - 1)];
-      fence_proxy_async();
-      mbar_expect_tx(b, sz);
-      bulk_g2s(ring + (uint32_t)((s & (NS - 1)) << p.slot_log2), p.K + lo, sz, b);
-    }
-  };
-  auto wait_slot = [&](int64_t s) {
-    const int64_t lo = sbase + (s << p.slot_log2);
-    if (lo < bulk_lim) {
-      bool ok = mbar_wait_bounded(&bar[s & (NS - 1)], (uint32_t)((s >> p.ns_log2) & 1));
-      if (!__all_sync(0xffffffffu, ok)) {
-        if (lane == 0) {
-          atomicExch(&reinterpret_cast<WsHeader *>(p.status)->status, TK_ETIMEOUT);
-          reinterpret_cast<WsHeader *>(p.status)->where = 1;
-        }
-        failed = true;
+      hdr->nb[bi] = nb;
+      hdr->piece[bi] = piece_p;
+      if (b1 > b0) {
+        fence_proxy_async();
+        mbar_expect_tx(&hdr->bar[bi], (uint32_t)(b1 - b0));
+        bulk_g2s(bufs + (size_t)bi * p.buf_bytes, p.K + b0, (uint32_t)(b1 - b0), &hdr->bar[bi]);
       }
     }
-    // bytes past the last 16-byte boundary of the array are not reachable by
-    // the bulk engine: copy them with plain loads
-    if (rel1 > tail_lo && tail_lo >= lo && tail_lo < lo + (int64_t)SLOT) {
-      const int64_t nb = rel1 - tail_lo;
-      if (lane < nb) {
-        uint32_t ri = (uint32_t)((tail_lo + lane - sbase) & (RING - 1));
-        ring[ri] = p.K[tail_lo + lane];
-      }
-      __syncwarp();
+    cp += nb;
+    posp = pend;
+    if (cp == n && posp < endp) {
+      if (m > 2 && next_sorted(m - 2, n, Qp)) cp = Qp[m - 3];
     }
+    ++j_issue;
   };
-
-  if (have) {
-    for (int64_t s = 0; s < (int64_t)NS; ++s) issue(s);
-    s_issued = NS;
-  }
 
   // ------------------------------------------------------------ accumulators
   N acc[NC];
@@ -343,15 +387,15 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
     acc[k] = mk<CT, D>(CT(0), CT(0));
-    int e = 32 * k + lane;
+    const int e = 32 * k + lane;
     ar[k] = (e < n) ? alpha_at(n - 1 - e) : mk<CT, D>(CT(0), CT(0));
   }
   double S_v = 0.0, S_d = 0.0;
 
   // triangle state
-  int b = -1;           // last value of Q (-1: m = 2, no first row)
-  int kb = 0;           // multiplicity of b in Q
-  CT Mprime = CT(2), Mf = CT(2);
+  int b = -1;   // last value of Q (-1: m = 2, no first row)
+  int kb = 0;   // multiplicity of b in Q
+  CT Mprime = CT(2), Mf = CT(2), inv_first = CT(0.5);
   N AQ = mk<CT, D>(CT(1), CT(0));
   N cA = AQ, cAf = AQ;
   N Trest = mk<CT, D>(CT(0), CT(0)), Tfirst = Trest;
@@ -359,10 +403,9 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
 
   auto setup_triangle = [&]() {
     AQ = mk<CT, D>(CT(1), CT(0));
-    double fact_m = 1.0;
+    int fact_m = 1;
     for (int i = 2; i <= m; ++i) fact_m *= i;
-    double den = 1.0;
-    int run = 0;
+    int den = 1, run = 0;
     for (int j = 0; j < m - 2; ++j) {
       AQ = AQ * alpha_at(Q[j]);
       run = (j > 0 && Q[j] == Q[j - 1]) ? run + 1 : 1;
@@ -378,6 +421,7 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
     }
     Mprime = CT(fact_m / den);
     Mf = Mprime / CT(kb + 1);
+    inv_first = CT(1) / CT(kb + 2);
     cA = scale(Mprime * inv_m, AQ);
     cAf = scale(Mf * inv_m, AQ);
   };
@@ -405,7 +449,7 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
     __syncwarp();
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
-      int e = 32 * k + lane;
+      const int e = 32 * k + lane;
       if (e < n) {
         g_v[n - 1 - e] += acc[k].v;
         if (D) g_d[n - 1 - e] += acc[k].d;
@@ -417,87 +461,196 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
     Tfirst = Trest;
   };
 
-  if (have) setup_triangle();
-  int64_t pos = p_row;
-  bool open = have;  // a triangle is open (has unflushed rows)
+  for (int s = 0; s < NB - 1; ++s) issue_next();
+  bool open = false;
 
-  while (pos < p_end && !failed) {
-    // ---------------------------------------------------- batch of rows
-    int nb = 0;
-    int64_t pi[kRB];
-    int sl[kRB];
-    int64_t q = pos;
-#pragma unroll
-    for (int i = 0; i < kRB; ++i) {
-      pi[i] = q;
-      bool ok = (c + i < n) && (q < p_end);
-      sl[i] = ok ? n - 1 - c - i : 0;
-      if (ok) {
-        nb = i + 1;
-        q += n - c - i;
+  while (j_cons < j_issue && !failed) {
+    // ---------------------------------------------------- wait for this block
+    const int bi = (int)(j_cons % NB);
+    const uint32_t parity = (uint32_t)((j_cons / NB) & 1);
+    __syncwarp();
+    const int nb = hdr->nb[bi];
+    const int piece = hdr->piece[bi];
+    if (piece != piece_c) {
+      // this block starts a new piece: restart the compute cursor there
+      if (open) flush_triangle();
+      const WarpPlan &pl = p.plan[piece];
+      for (int j = 0; j < kMaxOrder; ++j) Q[j] = pl.t[j];
+      c = pl.t[m - 2];
+      pos = pl.start;
+      end = pl.end;
+      piece_c = piece;
+      setup_triangle();
+      open = true;
+    }
+    const int L0 = n - c;
+    const int64_t pend = pos + (int64_t)(nb * L0 - (nb * (nb - 1)) / 2);
+    const int64_t rb0 = (pos - p.off_lo) * ES;
+    const int64_t b0 = rb0 & ~int64_t(15);
+    const int64_t rb1 = (pend - p.off_lo) * ES;
+    const int64_t b1 = min((rb1 + 15) & ~int64_t(15), tail_lo);
+    unsigned char *buf = bufs + (size_t)bi * p.buf_bytes;
+    if (b1 > b0) {
+      const bool ok = mbar_wait_bounded(&hdr->bar[bi], parity);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) {
+          atomicExch(&reinterpret_cast<WsHeader *>(p.status)->status, TK_ETIMEOUT);
+          reinterpret_cast<WsHeader *>(p.status)->where = 1;
+        }
+        failed = true;
+        break;
       }
     }
-    const int64_t p_next = q;
-    const int64_t s_hi = ((p_next - p.off_lo) * ES - 1 - sbase) >> p.slot_log2;
-    if (s_hi >= s_issued) {  // batch larger than the ring: configuration error
-      if (lane == 0) {
-        atomicExch(&reinterpret_cast<WsHeader *>(p.status)->status, TK_EINVAL);
-        reinterpret_cast<WsHeader *>(p.status)->where = 2;
+    if (rb1 > tail_lo) {
+      // bytes past the last 16-byte boundary of the array: plain loads
+      const int64_t nt = rb1 - max(tail_lo, b0);
+      if (lane < nt) {
+        const int64_t src = max(tail_lo, b0) + lane;
+        buf[src - b0] = p.K[src];
       }
-      failed = true;
-      break;
     }
-    while (s_ready <= s_hi) wait_slot(s_ready++);
-    if (failed) break;
+    ++j_cons;
+    __syncwarp();
+    // the previous block's buffer is free again: keep NBUF-1 copies in flight
+    issue_next();
 
-    N cf[kRB];
-    uint32_t zl[kRB];
-#pragma unroll
-    for (int i = 0; i < kRB; ++i) {
-      const int ci = min(c + i, n - 1);
-      cf[i] = ((ci == b) ? cAf : cA) * alpha_at(ci);
-      zl[i] = (uint32_t)pi[i] + (uint32_t)sl[i] - (uint32_t)lane - ebase;
+    // ---------------------------------------------------- rows of the block
+    const ST *bp = reinterpret_cast<const ST *>(buf) + (int)((rb0 - b0) / ES);
+    if (lane < kRB) {
+      // row data, one lane per row
+      const int i = lane;
+      const bool live = i < nb;
+      const int cr = min(c + i, n - 1);
+      const N cfi = live ? ((cr == b) ? cAf : cA) * alpha_at(cr) : mk<CT, D>(CT(0), CT(0));
+      RowInfo<CT> ri;
+      ri.cf_v = cfi.v;
+      ri.cf_d = cfi.d;
+      // rows past the block's end read row 0's (finite) entries with a zero
+      // coefficient, so the unmasked chunks stay harmless
+      ri.rowend = live ? (L0 - 1) + i * L0 - (i * (i + 1)) / 2 : L0 - 1;
+      ri.sl = live ? L0 - i - 1 : 0;
+      rinfo[i] = ri;
     }
-    N dot[kRB];
+    __syncwarp();
+    for (int r = 0; r < nb; r += 4) {
+      // four rows at a time: their lengths differ by at most 3, so the chunk
+      // count of the longest serves all four; only its top two chunks can run
+      // past a row's end and need masks
+      N cf[4], dot[4];
+      int sl[4];
+      const ST *prow[4];
 #pragma unroll
-    for (int i = 0; i < kRB; ++i) dot[i] = mk<CT, D>(CT(0), CT(0));
-
+      for (int i = 0; i < 4; ++i) {
+        const RowInfo<CT> ri = rinfo[r + i];
+        cf[i] = mk<CT, D>(ri.cf_v, ri.cf_d);
+        sl[i] = ri.sl;
+        prow[i] = bp + (ri.rowend - lane);
+        dot[i] = mk<CT, D>(CT(0), CT(0));
+      }
+      // enter at the top chunk (two masked chunks), continue down the
+      // unmasked chain to chunk 0
+      switch ((sl[0] + 31) >> 5) {
+        case 1: quad_chunk<0, true>(acc, dot, ar, prow, sl, lane, cf); goto chunks_done;
+        case 2: quad_chunk<1, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<0, true>(acc, dot, ar, prow, sl, lane, cf); goto chunks_done;
+        case 3: quad_chunk<2, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<1, true>(acc, dot, ar, prow, sl, lane, cf); goto full_0;
+        case 4: quad_chunk<3, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<2, true>(acc, dot, ar, prow, sl, lane, cf); goto full_1;
+        case 5: quad_chunk<4, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<3, true>(acc, dot, ar, prow, sl, lane, cf); goto full_2;
+        case 6: quad_chunk<5, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<4, true>(acc, dot, ar, prow, sl, lane, cf); goto full_3;
+        case 7: quad_chunk<6, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<5, true>(acc, dot, ar, prow, sl, lane, cf); goto full_4;
+        case 8: quad_chunk<7, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<6, true>(acc, dot, ar, prow, sl, lane, cf); goto full_5;
+        case 9: quad_chunk<8, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<7, true>(acc, dot, ar, prow, sl, lane, cf); goto full_6;
+        case 10: quad_chunk<9, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<8, true>(acc, dot, ar, prow, sl, lane, cf); goto full_7;
+        case 11: quad_chunk<10, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<9, true>(acc, dot, ar, prow, sl, lane, cf); goto full_8;
+        case 12: quad_chunk<11, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<10, true>(acc, dot, ar, prow, sl, lane, cf); goto full_9;
+        case 13: quad_chunk<12, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<11, true>(acc, dot, ar, prow, sl, lane, cf); goto full_10;
+        case 14: quad_chunk<13, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<12, true>(acc, dot, ar, prow, sl, lane, cf); goto full_11;
+        case 15: quad_chunk<14, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<13, true>(acc, dot, ar, prow, sl, lane, cf); goto full_12;
+        case 16: quad_chunk<15, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<14, true>(acc, dot, ar, prow, sl, lane, cf); goto full_13;
+        case 17: quad_chunk<16, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<15, true>(acc, dot, ar, prow, sl, lane, cf); goto full_14;
+        case 18: quad_chunk<17, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<16, true>(acc, dot, ar, prow, sl, lane, cf); goto full_15;
+        case 19: quad_chunk<18, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<17, true>(acc, dot, ar, prow, sl, lane, cf); goto full_16;
+        case 20: quad_chunk<19, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<18, true>(acc, dot, ar, prow, sl, lane, cf); goto full_17;
+        case 21: quad_chunk<20, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<19, true>(acc, dot, ar, prow, sl, lane, cf); goto full_18;
+        case 22: quad_chunk<21, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<20, true>(acc, dot, ar, prow, sl, lane, cf); goto full_19;
+        case 23: quad_chunk<22, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<21, true>(acc, dot, ar, prow, sl, lane, cf); goto full_20;
+        case 24: quad_chunk<23, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<22, true>(acc, dot, ar, prow, sl, lane, cf); goto full_21;
+        case 25: quad_chunk<24, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<23, true>(acc, dot, ar, prow, sl, lane, cf); goto full_22;
+        case 26: quad_chunk<25, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<24, true>(acc, dot, ar, prow, sl, lane, cf); goto full_23;
+        case 27: quad_chunk<26, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<25, true>(acc, dot, ar, prow, sl, lane, cf); goto full_24;
+        case 28: quad_chunk<27, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<26, true>(acc, dot, ar, prow, sl, lane, cf); goto full_25;
+        case 29: quad_chunk<28, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<27, true>(acc, dot, ar, prow, sl, lane, cf); goto full_26;
+        case 30: quad_chunk<29, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<28, true>(acc, dot, ar, prow, sl, lane, cf); goto full_27;
+        case 31: quad_chunk<30, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<29, true>(acc, dot, ar, prow, sl, lane, cf); goto full_28;
+        case 32: quad_chunk<31, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<30, true>(acc, dot, ar, prow, sl, lane, cf); goto full_29;
+        default: goto chunks_done;
+      }
+    full_29: quad_chunk<29, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_28: quad_chunk<28, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_27: quad_chunk<27, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_26: quad_chunk<26, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_25: quad_chunk<25, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_24: quad_chunk<24, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_23: quad_chunk<23, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_22: quad_chunk<22, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_21: quad_chunk<21, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_20: quad_chunk<20, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_19: quad_chunk<19, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_18: quad_chunk<18, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_17: quad_chunk<17, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_16: quad_chunk<16, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_15: quad_chunk<15, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_14: quad_chunk<14, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_13: quad_chunk<13, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_12: quad_chunk<12, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_11: quad_chunk<11, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_10: quad_chunk<10, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_9: quad_chunk<9, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_8: quad_chunk<8, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_7: quad_chunk<7, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_6: quad_chunk<6, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_5: quad_chunk<5, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_4: quad_chunk<4, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_3: quad_chunk<3, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_2: quad_chunk<2, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_1: quad_chunk<1, false>(acc, dot, ar, prow, sl, lane, cf);
+    full_0: quad_chunk<0, false>(acc, dot, ar, prow, sl, lane, cf);
+    chunks_done:
+      {
+        const int a = dsm_index(lane, r);
+        if (sizeof(CT) == 4) {
+          *reinterpret_cast<float4 *>(&dsm_v[a]) = make_float4(dot[0].v, dot[1].v, dot[2].v, dot[3].v);
+          if (D) *reinterpret_cast<float4 *>(&dsm_d[a]) = make_float4(dot[0].d, dot[1].d, dot[2].d, dot[3].d);
+        } else {
 #pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      if (32 * k >= sl[0]) break;
-      const int e = 32 * k + lane;
-#pragma unroll
-      for (int i = 0; i < kRB; ++i) {
-        if (e < sl[i]) {
-          const CT x = ld_ring<ST, CT>(ring, (zl[i] - 32u * k) & emask);
-          fma_acc(acc[k], x, cf[i]);
-          fma_acc(dot[i], x, ar[k]);
+          for (int i = 0; i < 4; ++i) {
+            dsm_v[a + i] = dot[i].v;
+            if (D) dsm_d[a + i] = dot[i].d;
+          }
         }
       }
     }
+    __syncwarp();
 
-    // reduce-scatter the 4 row dots: row i ends up on lanes 8i..8i+7
+    // ---------------------------------------------------- row dots and epilogue
     {
-      const bool h16 = lane & 16;
-      N k0 = sel(h16, dot[2], dot[0]), k1 = sel(h16, dot[3], dot[1]);
-      N s0 = sel(h16, dot[0], dot[2]), s1 = sel(h16, dot[1], dot[3]);
-      k0 = k0 + shfl_xor(s0, 16);
-      k1 = k1 + shfl_xor(s1, 16);
-      const bool h8 = lane & 8;
-      N kk = sel(h8, k1, k0), ss = sel(h8, k0, k1);
-      kk = kk + shfl_xor(ss, 8);
-      kk = kk + shfl_xor(kk, 4);
-      kk = kk + shfl_xor(kk, 2);
-      kk = kk + shfl_xor(kk, 1);
-      const int i = lane >> 3;
-      if ((lane & 7) == 0 && i < nb) {
-        const int ci = c + i;
+      const int r = lane & 15, h = lane >> 4;
+      N s = mk<CT, D>(CT(0), CT(0));
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int a = dsm_index(16 * h + i, r);
+        s.v += dsm_v[a];
+        if (D) s.d += dsm_d[a];
+      }
+      s = s + shfl_xor(s, 16);
+      if (h == 0 && r < nb) {
+        const int ci = c + r;
         const N ac = alpha_at(ci);
-        const CT h = ld_ring<ST, CT>(ring, ((uint32_t)pi[i] - ebase) & emask);
+        const int head = r * L0 - (r * (r - 1)) / 2;  // index of row r's head
+        const CT hv = ld_elem<ST, CT>(bp + head);
         const bool first = (ci == b);
         const CT cnt = first ? CT(kb + 1) : CT(1);
-        const N Rf = kk + scale(h / (cnt + CT(1)), ac);
-        const N gadd = (first ? cAf : cA) * (scale(h, ac) + scale(cnt, kk));
+        const N Rf = s + scale(hv * (first ? inv_first : CT(0.5)), ac);
+        const N gadd = (first ? cAf : cA) * (scale(hv, ac) + scale(cnt, s));
         g_v[ci] += gadd.v;
         if (D) g_d[ci] += gadd.d;
         const N tadd = scale(first ? Mf : Mprime, ac * Rf);
@@ -507,11 +660,11 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
 
     // ---------------------------------------------------- advance
     c += nb;
-    pos = p_next;
+    pos = pend;
     if (c == n) {
       flush_triangle();
       open = false;
-      if (pos < p_end) {
+      if (pos < end) {
         if (m > 2 && next_sorted(m - 2, n, Q)) {
           c = Q[m - 3];
           setup_triangle();
@@ -521,16 +674,13 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
         }
       }
     }
-    __syncwarp();
-    const int64_t s_free = ((pos - p.off_lo) * ES - sbase) >> p.slot_log2;
-    while (s_issued < s_free + (int64_t)NS) issue(s_issued++);
   }
   if (open) flush_triangle();
-  // drain bulk copies still in flight before the block can exit
-  while (s_ready < s_issued) {
-    const int64_t lo = sbase + (s_ready << p.slot_log2);
-    if (lo < bulk_lim) mbar_wait_bounded(&bar[s_ready & (NS - 1)], (uint32_t)((s_ready >> p.ns_log2) & 1));
-    ++s_ready;
+  // drain copies still in flight before the block can exit
+  while (j_cons < j_issue) {
+    const int bi = (int)(j_cons % NB);
+    mbar_wait_bounded(&hdr->bar[bi], (uint32_t)((j_cons / NB) & 1));
+    ++j_cons;
   }
   __syncwarp();
 
@@ -546,7 +696,8 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
   for (int l = threadIdx.x; l < n; l += blockDim.x) {
     double sv = 0.0, sd = 0.0;
     for (int ww = 0; ww < p.warps; ++ww) {
-      const CT *gw = reinterpret_cast<const CT *>(smem + p.vec_bytes + (size_t)ww * p.warp_bytes + 128 + RING);
+      const CT *gw = reinterpret_cast<const CT *>(smem + p.vec_bytes + (size_t)ww * p.warp_bytes +
+                                                  warp_fixed_bytes<CT, D>());
       sv += (double)gw[l];
       if (D) sd += (double)gw[n + l];
     }

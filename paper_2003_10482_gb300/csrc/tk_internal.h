@@ -23,11 +23,24 @@ int cuda_fail(cudaError_t e, const char *what);
 // Layout of every workspace: a 256-byte header (status word and reserved
 // counters) followed by the per-block partial sums of the contraction.
 struct WsHeader {
-  int status;        // TK_OK or TK_ETIMEOUT, set by kernels, read by tk_status_read
-  int where;         // which wait ran out (diagnostic)
-  int pad[62];
+  int status;                 // TK_OK or TK_ETIMEOUT, set by kernels, read by tk_status_read
+  int where;                  // which wait ran out (diagnostic)
+  unsigned long long ticket;  // next piece of the contraction to hand out
+  int pad[60];
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
+
+// Work of one warp of the contraction: rows [start, end) (row-aligned
+// offsets); t[0..m-3] is the prefix Q of the first row, t[m-2] its c.
+struct WarpPlan {
+  int64_t start, end;
+  int32_t t[kMaxOrder];
+};
+static_assert(sizeof(WarpPlan) == 48, "plan record");
+
+// Row-aligned cut of [lo, hi) into `pieces` near-equal-cost pieces.
+void build_plan(int m, int n, int64_t lo, int64_t hi, int pieces, int64_t row_cost, int64_t tri_cost,
+                WarpPlan *out);
 
 // Device properties cached per device.
 struct DevInfo {
@@ -46,18 +59,19 @@ struct ContractArgs {
   int vec_dtype;    // dtype of alpha / v
   const void *alpha;
   const void *v;    // non-NULL: dual pass (HVP)
-  double *part;     // per-block partials (workspace)
+  void *work;       // workspace: header, plan region, per-block partials
   int *status;      // workspace status word
-  // tuning (0 = default)
-  int warps;
-  int slot_log2;
-  int ns_log2;
-  int ctas_per_sm;
 };
 
 // Launch the main pass; the partial sums land in args.part (layout
 // part[block][vec][n + 2]: vec 0 = value, vec 1 = derivative; entry n = S).
-int contract_pass(const ContractArgs &a, int *grid_out, cudaStream_t st);
+int contract_pass(const ContractArgs &a, int *grid_out, const double **part_out, cudaStream_t st);
+
+// Process-wide overrides of the contraction launch configuration.
+extern tk_contract_config g_contract_cfg;
+// Resolve the configuration of a pass (no launch); fills the kernel's ring,
+// warps and grid parameters.
+int contract_resolve(int m, int n, int storage, bool dual, tk_contract_config *out, int *grid);
 
 // Sum the per-block partials of one pass into outputs (FP64, fixed order).
 //   mode 0: G = value part (vec_dtype), S
@@ -79,7 +93,10 @@ struct FinalizeArgs {
 };
 int contract_finalize(const FinalizeArgs &f, cudaStream_t st);
 
+// Bytes of the workspace regions (plan records for every warp of the largest
+// launch, then the per-block partial sums).
+size_t contract_plan_bytes(int sms);
 size_t contract_part_bytes(int n, int grid);
-int contract_default_grid();
+size_t contract_workspace_bytes(int n, int sms);
 
 }  // namespace tk

@@ -7,7 +7,7 @@ import oracle
 
 U32 = 2.0 ** -24   # unit roundoff of FP32
 U64 = 2.0 ** -53
-UBF16 = 2.0 ** -9  # unit roundoff of BF16 (8-bit significand)
+UBF16 = 2.0 ** -8  # unit roundoff of BF16 (8-bit significand incl. the implicit bit)
 
 TORCH = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}
 

@@ -74,3 +74,36 @@ def test_row_align(L):
     for off in range(N + 1):
         want = min(s for s in starts if s >= off)
         assert tk.tk_row_align(m, n, off) == want
+
+
+def _row_costs(m, n, lo, hi, rc, tc):
+    """(offset, cost) of every row start in [lo, hi), by enumeration."""
+    tuples = oracle.enumerate_tuples(m, n)
+    rows = []
+    prev_q = None
+    for o in range(lo, hi):
+        t = tuples[o]
+        if t[-1] == t[-2]:
+            q = tuple(t[:-2])
+            cost = (n - t[-2]) + rc + (tc if q != prev_q else 0)
+            rows.append((o, cost))
+            prev_q = q
+    return rows
+
+
+@pytest.mark.parametrize("m,n,pieces", [(4, 9, 7), (2, 30, 5), (6, 6, 13), (4, 12, 40), (3, 10, 3)])
+def test_contract_plan_is_row_aligned_and_balanced(L, m, n, pieces):
+    N = tk.tk_packed_size(m, n)
+    for lo, hi in ((0, N), (tk.tk_row_align(m, n, N // 3), tk.tk_row_align(m, n, (2 * N) // 3))):
+        rc, tc = 5, 11
+        b = tk.tk_contract_plan(m, n, lo, hi, pieces, rc, tc)
+        assert b[0] == lo and b[-1] == hi and len(b) == pieces + 1
+        assert all(x <= y for x, y in zip(b[:-1], b[1:]))
+        rows = _row_costs(m, n, lo, hi, rc, tc)
+        starts = {o for o, _ in rows} | {hi}
+        assert all(x in starts for x in b)
+        total = sum(c for _, c in rows)
+        big = max(c for _, c in rows) if rows else 0
+        for x, y in zip(b[:-1], b[1:]):
+            piece = sum(c for o, c in rows if x <= o < y)
+            assert piece <= total / pieces + big + tc
