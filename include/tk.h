@@ -205,6 +205,16 @@ int tk_objective(int m, int64_t n, int storage_dtype, const void *K, int64_t B,
                  double *grad, double *gnorm, void *work, size_t work_bytes,
                  void *stream);
 
+/* Dual objective and gradient from contractions that were already reduced
+ * (for instance summed over the shards of several devices):
+ *   F[b] = S[b]/m + (lambda_b/2)|A_b|^2 - <y, A_b>,  grad[b] = G[b] + lambda_b A_b - y,
+ *   gnorm[b] = |grad[b]|_2   (Section 4, eqs. dual_tensor_kernel and jq).
+ * G: B x n FP64 (K[A_b^{m-1}]), S: B FP64 (K[A_b^m]); everything FP64 on the
+ * device.  grad and gnorm may be NULL.  No workspace. */
+int tk_assemble_objective(int m, int64_t n, int64_t B, const double *G, const double *S, const double *A,
+                          const double *y, const double *lambda, double *F, double *grad, double *gnorm,
+                          void *stream);
+
 #ifdef __cplusplus
 }
 #endif

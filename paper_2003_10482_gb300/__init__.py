@@ -76,6 +76,7 @@ def _declare(L):
         "tk_contract_get_config": (i32, [i32, i64, i32, i32, P]),
         "tk_contract_plan": (i32, [i32, i64, i64, i64, i32, i32, i32, P]),
         "tk_objective": (i32, [i32, i64, i32, P, i64, P, P, P, P, P, P, P, sz, P]),
+        "tk_assemble_objective": (i32, [i32, i64, i64, P, P, P, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         if hasattr(L, name):
@@ -281,4 +282,23 @@ def tk_objective(K: torch.Tensor, m: int, n: int, A: torch.Tensor, y: torch.Tens
     _check(lib().tk_objective(m, n, dtype_code(K.dtype), _p(K), B, _p(A2),
                               _p(y.to(torch.float64).contiguous()), _p(lam_t), _p(F), _p(grad),
                               _p(gn), _p(work), work.numel(), _stream(stream)))
+    return F, grad.reshape(A.shape), gn
+
+
+def tk_assemble_objective(m: int, n: int, G: torch.Tensor, S: torch.Tensor, A: torch.Tensor,
+                          y: torch.Tensor, lam, stream=None):
+    """(F, grad, gnorm) from reduced contractions G = K[A^{m-1}] (B x n) and S = K[A^m] (B)."""
+    G2 = G.reshape(-1, n).to(torch.float64).contiguous()
+    B = G2.shape[0]
+    A2 = A.reshape(B, n).to(torch.float64).contiguous()
+    S2 = S.reshape(B).to(torch.float64).contiguous()
+    lam_t = torch.as_tensor(lam, dtype=torch.float64, device=G.device).reshape(-1)
+    if lam_t.numel() == 1 and B > 1:
+        lam_t = lam_t.expand(B).contiguous()
+    F = torch.empty(B, dtype=torch.float64, device=G.device)
+    gn = torch.empty(B, dtype=torch.float64, device=G.device)
+    grad = torch.empty_like(A2)
+    _check(lib().tk_assemble_objective(m, n, B, _p(G2), _p(S2), _p(A2),
+                                       _p(y.to(torch.float64).contiguous()), _p(lam_t), _p(F),
+                                       _p(grad), _p(gn), _stream(stream)))
     return F, grad.reshape(A.shape), gn
