@@ -187,6 +187,27 @@ int tk_contract_get_config(int m, int64_t n, int storage_dtype, int dual, tk_con
 int tk_contract_plan(int m, int64_t n, int64_t off_lo, int64_t off_hi, int pieces, int row_cost,
                      int tri_cost, int64_t *bounds_host);
 
+/* K[a^{m-1}] and K[a^m] of one dual vector, like tk_contract with B = 1 and
+ * r = m-1, for callers that cannot allocate device memory (code running under
+ * CUDA graph capture, runtimes with pre-reserved memory, hosts that only lend
+ * the library their own tensors).  The thesis has no counterpart.  The caller
+ * passes K, alpha (n values of vec_dtype), G (n values of vec_dtype) and S
+ * (one FP64 value, may be NULL), all device pointers; no workspace.
+ *
+ * Scratch lives in a static 8 MiB device array inside the library, held by
+ * every GPU that loads it until the process exits; the contraction's needs
+ * (status header, work plan, per-block partials) must fit in it, else
+ * TK_ENOMEM with the size it would need.  No cudaMalloc, cudaFree or other
+ * allocator is called.  The first call on a device looks the array up
+ * (cudaGetSymbolAddress), zeroes its header and uploads the work plan, and
+ * later calls upload a plan only when (m, n) or the configuration changes:
+ * make the first call for a given shape before any stream capture.  Every
+ * call on a device shares the array and leaves the last call's contents in
+ * it; calls whose executions overlap on the GPU (other streams, other host
+ * threads' streams) race on it and must be serialised by the caller. */
+int tk_contract_noalloc(int m, int64_t n, int storage_dtype, const void *K, int vec_dtype, const void *alpha,
+                        void *G, double *S, void *stream);
+
 /* Reads (and clears) the device-side status word of a workspace: TK_OK, or
  * TK_ETIMEOUT if a bounded wait of an earlier call on it ran out.  Synchronises
  * `stream`. */

@@ -77,6 +77,7 @@ def _declare(L):
         "tk_contract_plan": (i32, [i32, i64, i64, i64, i32, i32, i32, P]),
         "tk_objective": (i32, [i32, i64, i32, P, i64, P, P, P, P, P, P, P, sz, P]),
         "tk_assemble_objective": (i32, [i32, i64, i64, P, P, P, P, P, P, P, P, P]),
+        "tk_contract_noalloc": (i32, [i32, i64, i32, P, i32, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         if hasattr(L, name):
@@ -302,3 +303,12 @@ def tk_assemble_objective(m: int, n: int, G: torch.Tensor, S: torch.Tensor, A: t
                                        _p(y.to(torch.float64).contiguous()), _p(lam_t), _p(F),
                                        _p(grad), _p(gn), _stream(stream)))
     return F, grad.reshape(A.shape), gn
+
+
+def tk_contract_noalloc(K: torch.Tensor, m: int, n: int, alpha: torch.Tensor, G: torch.Tensor,
+                        S: torch.Tensor | None = None, stream=None):
+    """K[alpha^{m-1}] into G and K[alpha^m] into S without any device allocation by the
+    library (its scratch is a static device array); G and S are caller-owned."""
+    _check(lib().tk_contract_noalloc(m, n, dtype_code(K.dtype), _p(K), dtype_code(alpha.dtype),
+                                     _p(alpha), _p(G), _p(S), _stream(stream)))
+    return G, S

@@ -316,6 +316,59 @@ int contract_pass(const ContractArgs &a, int *grid_out, const double **part_out,
   return contract_launch_bf16(kp, dual, r.nc, r.grid, r.warps * 32, r.smem, st);
 }
 
+int contract_pass_static(const ContractArgs &a, WarpPlan *host_plan, int host_cap, StaticPlanState *state,
+                         size_t scratch_bytes, int *grid_out, const double **part_out, cudaStream_t st) {
+  const bool dual = a.v != nullptr;
+  Resolved r;
+  int rc = resolve(a.m, a.n, a.storage, dual, &r);
+  if (rc != TK_OK) return rc;
+  const int pieces = r.ppw * r.grid * r.warps;
+  const size_t plan_bytes = (size_t)pieces * sizeof(WarpPlan);
+  const size_t need = sizeof(WsHeader) + plan_bytes + contract_part_bytes(a.n, r.grid);
+  if (pieces > host_cap || need > scratch_bytes)
+    return fail(TK_ENOMEM, "contraction needs %zu bytes of scratch (%d plan records); the static scratch holds %zu",
+                need, pieces, scratch_bytes);
+  unsigned char *ws = reinterpret_cast<unsigned char *>(a.work);
+  WarpPlan *plan = reinterpret_cast<WarpPlan *>(ws + sizeof(WsHeader));
+  double *part = reinterpret_cast<double *>(ws + sizeof(WsHeader) + plan_bytes);
+  if (!(state->valid && state->m == a.m && state->n == a.n && state->lo == a.off_lo && state->hi == a.off_hi &&
+        state->pieces == pieces && state->rc == r.row_cost && state->tc == r.tri_cost)) {
+    build_plan(a.m, a.n, a.off_lo, a.off_hi, pieces, r.row_cost, r.tri_cost, host_plan);
+    TK_CUDA_CHECK(cudaMemcpyAsync(plan, host_plan, plan_bytes, cudaMemcpyHostToDevice, st));
+    // the host records are reused by the next rebuild: wait for the copy
+    TK_CUDA_CHECK(cudaStreamSynchronize(st));
+    *state = StaticPlanState{1, a.m, a.n, a.off_lo, a.off_hi, pieces, r.row_cost, r.tri_cost};
+  }
+  WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
+  TK_CUDA_CHECK(cudaMemsetAsync(&hdr->ticket, 0, sizeof(hdr->ticket), st));
+  KParams kp;
+  kp.m = a.m;
+  kp.n = a.n;
+  kp.K = reinterpret_cast<const unsigned char *>(a.K);
+  kp.off_lo = a.off_lo;
+  kp.off_hi = a.off_hi;
+  kp.bytes = (a.off_hi - a.off_lo) * dtype_size(a.storage);
+  kp.alpha = a.alpha;
+  kp.v = a.v;
+  kp.vec_dtype = a.vec_dtype;
+  kp.part = part;
+  kp.status = a.status;
+  kp.plan = plan;
+  kp.pieces = pieces;
+  kp.ticket = &hdr->ticket;
+  kp.warps = r.warps;
+  kp.nbuf = r.nbuf;
+  kp.buf_bytes = r.buf_bytes;
+  kp.cap = r.cap;
+  kp.vec_bytes = r.vec_bytes;
+  kp.warp_bytes = r.warp_bytes;
+  if (grid_out) *grid_out = r.grid;
+  if (part_out) *part_out = part;
+  if (a.storage == TK_F64) return contract_launch_f64(kp, dual, r.nc, r.grid, r.warps * 32, r.smem, st);
+  if (a.storage == TK_F32) return contract_launch_f32(kp, dual, r.nc, r.grid, r.warps * 32, r.smem, st);
+  return contract_launch_bf16(kp, dual, r.nc, r.grid, r.warps * 32, r.smem, st);
+}
+
 int contract_finalize(const FinalizeArgs &f, cudaStream_t st) {
   finalize_kernel<<<1, 256, 0, st>>>(f);
   TK_CUDA_CHECK(cudaGetLastError());

@@ -73,6 +73,22 @@ extern tk_contract_config g_contract_cfg;
 // warps and grid parameters.
 int contract_resolve(int m, int n, int storage, bool dual, tk_contract_config *out, int *grid);
 
+// Plan state kept by a caller that owns a fixed scratch region: which plan
+// (m, n, range, pieces, costs) its plan region currently holds.
+struct StaticPlanState {
+  int valid;
+  int m, n;
+  int64_t lo, hi;
+  int pieces, rc, tc;
+};
+
+// Same pass as contract_pass, on a fixed scratch region of `scratch_bytes`
+// bytes (header, plan region, partials laid out as in a workspace).  The plan
+// is built into host_plan (capacity host_cap records; no host or device
+// allocation) and uploaded only when it differs from *state.
+int contract_pass_static(const ContractArgs &a, WarpPlan *host_plan, int host_cap, StaticPlanState *state,
+                         size_t scratch_bytes, int *grid_out, const double **part_out, cudaStream_t st);
+
 // Sum the per-block partials of one pass into outputs (FP64, fixed order).
 //   mode 0: G = value part (vec_dtype), S
 //   mode 1: G = derivative part / (m-1)  (HVP)
