@@ -177,21 +177,13 @@ static int contract_impl(int m, int64_t n, int storage, const void *K, int64_t o
     a.v = (r == m - 2) ? reinterpret_cast<const unsigned char *>(V) + b * n * vs : nullptr;
     a.work = wsb;
     a.status = reinterpret_cast<int *>(wsb);
+    a.fin.mode = (r == m - 1) ? 0 : 1;
+    a.fin.out_dtype = vec_dtype;
+    a.fin.G = reinterpret_cast<unsigned char *>(G) + b * n * vs;
+    a.fin.S = (S && r == m - 1) ? S + b : nullptr;
     int grid = 0;
     const double *part = nullptr;
     rc = contract_pass(a, &grid, &part, st);
-    if (rc != TK_OK) return rc;
-    FinalizeArgs f;
-    memset(&f, 0, sizeof(f));
-    f.mode = (r == m - 1) ? 0 : 1;
-    f.m = m;
-    f.n = (int)n;
-    f.grid = grid;
-    f.part = part;
-    f.out_dtype = vec_dtype;
-    f.G = reinterpret_cast<unsigned char *>(G) + b * n * vs;
-    f.S = (S && r == m - 1) ? S + b : nullptr;
-    rc = contract_finalize(f, st);
     if (rc != TK_OK) return rc;
   }
   return TK_OK;
@@ -296,24 +288,16 @@ int tk_objective(int m, int64_t n, int storage, const void *K, int64_t B, const 
     a.alpha = A + b * n;
     a.work = wsb;
     a.status = reinterpret_cast<int *>(wsb);
+    a.fin.mode = 2;
+    a.fin.alpha = A + b * n;
+    a.fin.y = y;
+    a.fin.lambda = lambda + b;
+    a.fin.F = F ? F + b : nullptr;
+    a.fin.grad = grad ? grad + b * n : nullptr;
+    a.fin.gnorm = gnorm ? gnorm + b : nullptr;
     int grid = 0;
     const double *part = nullptr;
     rc = contract_pass(a, &grid, &part, st);
-    if (rc != TK_OK) return rc;
-    FinalizeArgs f;
-    memset(&f, 0, sizeof(f));
-    f.mode = 2;
-    f.m = m;
-    f.n = (int)n;
-    f.grid = grid;
-    f.part = part;
-    f.alpha = A + b * n;
-    f.y = y;
-    f.lambda = lambda + b;
-    f.F = F ? F + b : nullptr;
-    f.grad = grad ? grad + b * n : nullptr;
-    f.gnorm = gnorm ? gnorm + b : nullptr;
-    rc = contract_finalize(f, st);
     if (rc != TK_OK) return rc;
   }
   return TK_OK;

@@ -241,7 +241,8 @@ static int resolve(int m, int n, int storage, bool dual, Resolved *r) {
   r->warp_bytes = (r->warp_bytes + 127) & ~127;
   r->cps = o.ctas_per_sm > 0 ? o.ctas_per_sm : 1;
   if (r->cps > 2) return fail(TK_EINVAL, "ctas_per_sm must be 1 or 2");
-  const int smem_budget = (di.smem_optin - 1024) / r->cps;
+  // keep 4 KB for the kernel's static shared memory (warp S partials, final reduction)
+  const int smem_budget = (di.smem_optin - 4096) / r->cps;
   const int warps_fit = (smem_budget - r->vec_bytes) / r->warp_bytes;
   int warps = o.warps > 0 ? o.warps : kMaxWarps;
   warps = std::min(warps, max_threads_est(cts, dual, r->nc) / 32);
@@ -287,7 +288,7 @@ int contract_pass(const ContractArgs &a, int *grid_out, const double **part_out,
   rc = ensure_plan(key, plan, st);
   if (rc != TK_OK) return rc;
   WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
-  TK_CUDA_CHECK(cudaMemsetAsync(&hdr->ticket, 0, sizeof(hdr->ticket), st));
+  TK_CUDA_CHECK(cudaMemsetAsync(&hdr->ticket, 0, sizeof(hdr->ticket) + sizeof(hdr->done), st));
   KParams kp;
   kp.m = a.m;
   kp.n = a.n;
@@ -303,6 +304,12 @@ int contract_pass(const ContractArgs &a, int *grid_out, const double **part_out,
   kp.plan = plan;
   kp.pieces = pieces;
   kp.ticket = &hdr->ticket;
+  kp.done = &hdr->done;
+  kp.fin = a.fin;
+  kp.fin.part = part;
+  kp.fin.grid = r.grid;
+  kp.fin.m = a.m;
+  kp.fin.n = a.n;
   kp.warps = r.warps;
   kp.nbuf = r.nbuf;
   kp.buf_bytes = r.buf_bytes;
@@ -340,7 +347,7 @@ int contract_pass_static(const ContractArgs &a, WarpPlan *host_plan, int host_ca
     *state = StaticPlanState{1, a.m, a.n, a.off_lo, a.off_hi, pieces, r.row_cost, r.tri_cost};
   }
   WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
-  TK_CUDA_CHECK(cudaMemsetAsync(&hdr->ticket, 0, sizeof(hdr->ticket), st));
+  TK_CUDA_CHECK(cudaMemsetAsync(&hdr->ticket, 0, sizeof(hdr->ticket) + sizeof(hdr->done), st));
   KParams kp;
   kp.m = a.m;
   kp.n = a.n;
@@ -356,6 +363,12 @@ int contract_pass_static(const ContractArgs &a, WarpPlan *host_plan, int host_ca
   kp.plan = plan;
   kp.pieces = pieces;
   kp.ticket = &hdr->ticket;
+  kp.done = &hdr->done;
+  kp.fin = a.fin;
+  kp.fin.part = part;
+  kp.fin.grid = r.grid;
+  kp.fin.m = a.m;
+  kp.fin.n = a.n;
   kp.warps = r.warps;
   kp.nbuf = r.nbuf;
   kp.buf_bytes = r.buf_bytes;

@@ -201,6 +201,8 @@ struct KParams {
   const WarpPlan *plan;      // cost-balanced pieces of the range
   int pieces;
   unsigned long long *ticket;  // next piece to hand out (zeroed before the launch)
+  unsigned int *done;          // blocks finished (zeroed before the launch)
+  FinalizeArgs fin;            // outputs the last block writes
   int warps;
   int nbuf;         // linear staging buffers per warp
   int buf_bytes;    // bytes of one buffer (block budget + alignment slack)
@@ -272,6 +274,96 @@ __device__ __forceinline__ void quad_chunk(Nm<CT, D> (&acc)[NC], Nm<CT, D> (&dot
         fma_acc(dot[i], x, ar[K]);
       }
     }
+  }
+}
+
+// Sum of one column of the per-block partials over blocks b0, b0+step, ...
+// in increasing order, eight independent loads in flight (L2, not L1: the
+// partials were written by other blocks).
+__device__ __forceinline__ double sum_blocks(const double *col, int ld2, int grid, int b0, int step) {
+  double s = 0.0;
+  int b = b0;
+  for (; b + 7 * step < grid; b += 8 * step) {
+    double v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __ldcg(col + (size_t)(b + i * step) * ld2);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += v[i];
+  }
+  for (; b < grid; b += step) s += __ldcg(col + (size_t)b * ld2);
+  return s;
+}
+
+// Run by the last block of a pass: the fixed-order FP64 sum of every block's
+// partials, written as K[a^{m-1}] (mode 0), K[a^{m-2}, v] (mode 1, the
+// derivative part over m-1), or the dual objective F, its gradient and the
+// gradient norm (mode 2; F = S/m + lambda/2 |a|^2 - <y, a>, grad = g + lambda a - y).
+static __device__ void final_reduce(const FinalizeArgs &f, const double *part, int grid) {
+  __shared__ double red[3][32];
+  const int n = f.n, ld = n + 2, ld2 = 2 * ld;
+  const int vec = (f.mode == 1) ? 1 : 0;
+  const int nt = blockDim.x;
+  // split the blocks over several threads per column (a power of two, <= 8)
+  // when the columns are few
+  int per = 1;
+  while (per < 8 && 2 * per * (n + 1) <= nt) per <<= 1;
+  const int cols = (n + 1);
+  double ssq = 0.0, aa = 0.0, ya = 0.0;
+  __shared__ double S_tot;
+  for (int base = 0; base < cols; base += nt / per) {
+    const int t = threadIdx.x;
+    const int l = base + t / per, sub = t % per;
+    const bool act = (t / per) < nt / per && l < cols;
+    double s = act ? sum_blocks(part + vec * ld + l, ld2, grid, sub, per) : 0.0;
+    // fixed-order tree combine of the per-thread sub-sums of a column
+    for (int k = 1; k < per; k <<= 1) s += __shfl_down_sync(0xffffffffu, s, k, per);
+    if (act && sub == 0) {
+      if (l == n) {
+        if (f.mode != 1) S_tot = s;
+      } else if (f.mode == 2) {
+        const double a = f.alpha[l], gr = s + f.lambda[0] * a - f.y[l];
+        if (f.grad) f.grad[l] = gr;
+        ssq += gr * gr;
+        aa += a * a;
+        ya += f.y[l] * a;
+      } else {
+        const double v = (f.mode == 1) ? s / (double)(f.m - 1) : s;
+        if (f.out_dtype == TK_F64) reinterpret_cast<double *>(f.G)[l] = v;
+        else reinterpret_cast<float *>(f.G)[l] = (float)v;
+      }
+    }
+  }
+  __syncthreads();
+  if (f.mode == 0) {
+    if (threadIdx.x == 0 && f.S) f.S[0] = S_tot;
+    return;
+  }
+  if (f.mode == 1) return;
+  // fixed-order block sums of |grad|^2, |a|^2, <y, a>
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
+    aa += __shfl_xor_sync(0xffffffffu, aa, o);
+    ya += __shfl_xor_sync(0xffffffffu, ya, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = ssq;
+    red[1][wid] = aa;
+    red[2][wid] = ya;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t0 = 0, t1 = 0, t2 = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      t0 += red[0][w];
+      t1 += red[1][w];
+      t2 += red[2][w];
+    }
+    const double S = S_tot;
+    if (f.S) f.S[0] = S;
+    if (f.F) f.F[0] = S / f.m + 0.5 * f.lambda[0] * t1 - t2;
+    if (f.gnorm) f.gnorm[0] = sqrt(t0);
   }
 }
 
@@ -713,6 +805,16 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
     out[n] = sv;
     out[ld + n] = sd;
   }
+
+  // ------------------------------------------------------------ last block sums all blocks
+  __threadfence();
+  __syncthreads();
+  __shared__ int s_last;
+  if (threadIdx.x == 0) s_last = (atomicAdd(p.done, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  final_reduce(p.fin, p.part, gridDim.x);
 }
 
 // ------------------------------------------------------------------ launch

@@ -26,7 +26,8 @@ struct WsHeader {
   int status;                 // TK_OK or TK_ETIMEOUT, set by kernels, read by tk_status_read
   int where;                  // which wait ran out (diagnostic)
   unsigned long long ticket;  // next piece of the contraction to hand out
-  int pad[60];
+  unsigned int done;          // blocks of the current pass that have written their partials
+  int pad[59];
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
 
@@ -49,6 +50,24 @@ struct DevInfo {
 };
 int dev_info(DevInfo *out);
 
+// Sum the per-block partials of one pass into outputs (FP64, fixed order).
+//   mode 0: G = value part (vec_dtype), S
+//   mode 1: G = derivative part / (m-1)  (HVP)
+//   mode 2: objective: F, grad (FP64), gnorm with alpha/y/lambda
+struct FinalizeArgs {
+  int mode;
+  int m, n, grid;
+  const double *part;
+  int out_dtype;
+  void *G;
+  double *S;
+  const double *alpha;  // mode 2
+  const double *y;
+  const double *lambda;
+  double *F;
+  double *grad;
+  double *gnorm;
+};
 // One contraction pass of the single-vector kernel.
 struct ContractArgs {
   int m;
@@ -61,6 +80,7 @@ struct ContractArgs {
   const void *v;    // non-NULL: dual pass (HVP)
   void *work;       // workspace: header, plan region, per-block partials
   int *status;      // workspace status word
+  FinalizeArgs fin; // what the last block writes (part and grid are filled in by the pass)
 };
 
 // Launch the main pass; the partial sums land in args.part (layout
@@ -89,24 +109,6 @@ struct StaticPlanState {
 int contract_pass_static(const ContractArgs &a, WarpPlan *host_plan, int host_cap, StaticPlanState *state,
                          size_t scratch_bytes, int *grid_out, const double **part_out, cudaStream_t st);
 
-// Sum the per-block partials of one pass into outputs (FP64, fixed order).
-//   mode 0: G = value part (vec_dtype), S
-//   mode 1: G = derivative part / (m-1)  (HVP)
-//   mode 2: objective: F, grad (FP64), gnorm with alpha/y/lambda
-struct FinalizeArgs {
-  int mode;
-  int m, n, grid;
-  const double *part;
-  int out_dtype;
-  void *G;
-  double *S;
-  const double *alpha;  // mode 2
-  const double *y;
-  const double *lambda;
-  double *F;
-  double *grad;
-  double *gnorm;
-};
 int contract_finalize(const FinalizeArgs &f, cudaStream_t st);
 
 // Bytes of the workspace regions (plan records for every warp of the largest

@@ -9,6 +9,8 @@
 // work plan and per-block partial sums) lives in one file-scope device array
 // of fixed size that every GPU loading the library holds until the process
 // exits.  The thesis has no counterpart; it is an interface convenience.
+#include <string.h>
+
 #include <mutex>
 
 #include "tk_internal.h"
@@ -68,6 +70,7 @@ extern "C" int tk_contract_noalloc(int m, int64_t n, int storage, const void *K,
   if (rc != TK_OK) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   ContractArgs a;
+  memset(&a, 0, sizeof(a));
   a.m = m;
   a.n = (int)n;
   a.storage = storage;
@@ -79,25 +82,12 @@ extern "C" int tk_contract_noalloc(int m, int64_t n, int storage, const void *K,
   a.v = nullptr;
   a.work = scratch;
   a.status = reinterpret_cast<int *>(scratch);
+  a.fin.mode = 0;
+  a.fin.out_dtype = vec_dtype;
+  a.fin.G = G;
+  a.fin.S = S;
   int grid = 0;
   const double *part = nullptr;
-  rc = contract_pass_static(a, g_host_plan, kNoAllocPlanCap, &g_plan_state[dev], kNoAllocScratchBytes, &grid, &part,
-                            st);
-  if (rc != TK_OK) return rc;
-  FinalizeArgs f;
-  f.mode = 0;
-  f.m = m;
-  f.n = (int)n;
-  f.grid = grid;
-  f.part = part;
-  f.out_dtype = vec_dtype;
-  f.G = G;
-  f.S = S;
-  f.alpha = nullptr;
-  f.y = nullptr;
-  f.lambda = nullptr;
-  f.F = nullptr;
-  f.grad = nullptr;
-  f.gnorm = nullptr;
-  return contract_finalize(f, st);
+  return contract_pass_static(a, g_host_plan, kNoAllocPlanCap, &g_plan_state[dev], kNoAllocScratchBytes, &grid,
+                              &part, st);
 }
