@@ -236,6 +236,57 @@ int tk_assemble_objective(int m, int64_t n, int64_t B, const double *G, const do
                           const double *y, const double *lambda, double *F, double *grad, double *gnorm,
                           void *stream);
 
+/* ------------------------------------------------------------ dual solver */
+
+/* One or several dual problems over the same packed tensor (Section 4,
+ * eq. dual_tensor_kernel, lambda = 1/gamma):
+ *   min_a  K[a^m]/m + (lambda_b/2)|a|^2 - <y, a>,   a_i = 0 where mask_b[i] = 0.
+ * The objective is strongly convex (modulus lambda_b), so each problem has one
+ * minimiser whatever the algorithm; the thesis does not name its algorithm. */
+typedef struct {
+    int m;
+    int64_t n;
+    int storage_dtype;
+    const void *K;          /* N entries (device) */
+    const double *y;        /* n targets (device) */
+    int64_t B;              /* number of problems */
+    const double *lambda;   /* B regularisation weights (device) */
+    const uint8_t *mask;    /* B x n, 1 = point kept, 0 = held out (device); NULL = all kept */
+} tk_problem;
+
+typedef struct {
+    int method;             /* TK_NEWTON_CG (default) or TK_GD_BT */
+    double tol_gradnorm;    /* stop a problem when |grad F|_2 <= tol */
+    int max_iter;           /* outer iterations */
+    int max_cg;             /* conjugate-gradient steps per Newton step */
+    double armijo_c;        /* sufficient-decrease constant (0: 1e-4) */
+} tk_solve_opts;
+
+typedef struct {
+    int iters;              /* outer iterations taken */
+    int passes;             /* passes over the packed tensor (objective + HVP) */
+    double gradnorm;        /* final |grad F|_2 */
+    double F;               /* final objective */
+    int status;             /* TK_OK, TK_ENOTCONV (max_iter or no further decrease possible) */
+} tk_solve_report;
+
+/* Bytes of workspace tk_solve_dual needs. */
+size_t tk_solve_workspace_size(const tk_problem *P);
+
+/* Solves the B problems from the starting points in A_inout (B x n FP64,
+ * device; masked entries are zeroed), in FP64 vector arithmetic on the device:
+ *   Newton-CG:  H p = -grad F by conjugate gradients with forcing term
+ *               min(0.5, sqrt|grad F|), H v = (m-1) K[a^{m-2}, v] + lambda v,
+ *               then Armijo backtracking on F (halving the step);
+ *   GD_BT:      steepest descent with Armijo backtracking, step initialised
+ *               from the previous accepted step.
+ * Every objective is one contraction pass and every H v one dual-number pass
+ * (tk_contract with r = m-2).  Writes one report per problem (host array of
+ * B entries); returns TK_ENOTCONV if any problem missed tol.  Synchronises
+ * `stream` once per step to read the per-problem scalars. */
+int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double *A_inout, tk_solve_report *R_host,
+                  void *work, size_t work_bytes, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -78,6 +78,8 @@ def _declare(L):
         "tk_objective": (i32, [i32, i64, i32, P, i64, P, P, P, P, P, P, P, sz, P]),
         "tk_assemble_objective": (i32, [i32, i64, i64, P, P, P, P, P, P, P, P, P]),
         "tk_contract_noalloc": (i32, [i32, i64, i32, P, i32, P, P, P, P]),
+        "tk_solve_workspace_size": (sz, [P]),
+        "tk_solve_dual": (i32, [P, P, P, P, P, sz, P]),
     }
     for name, (res, args) in sig.items():
         if hasattr(L, name):
@@ -312,3 +314,54 @@ def tk_contract_noalloc(K: torch.Tensor, m: int, n: int, alpha: torch.Tensor, G:
     _check(lib().tk_contract_noalloc(m, n, dtype_code(K.dtype), _p(K), dtype_code(alpha.dtype),
                                      _p(alpha), _p(G), _p(S), _stream(stream)))
     return G, S
+
+
+class tk_problem(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int64), ("storage_dtype", ctypes.c_int),
+                ("K", ctypes.c_void_p), ("y", ctypes.c_void_p), ("B", ctypes.c_int64),
+                ("lam", ctypes.c_void_p), ("mask", ctypes.c_void_p)]
+
+
+class tk_solve_opts(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("tol_gradnorm", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("max_cg", ctypes.c_int), ("armijo_c", ctypes.c_double)]
+
+
+class tk_solve_report(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("passes", ctypes.c_int), ("gradnorm", ctypes.c_double),
+                ("F", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+_solve_ws: dict = {}
+
+
+def tk_solve_dual(K: torch.Tensor, m: int, n: int, y: torch.Tensor, lam, alpha0: torch.Tensor | None = None,
+                  mask: torch.Tensor | None = None, method: str = "newton_cg", tol: float = 1e-10,
+                  max_iter: int = 100, max_cg: int = 0, stream=None):
+    """Solve B dual problems over the packed tensor K.  Returns (alpha (B x n FP64),
+    reports (list of dicts), rc) where rc is TK_OK or TK_ENOTCONV."""
+    dev = K.device
+    lam_t = torch.as_tensor(lam, dtype=torch.float64, device=dev).reshape(-1).contiguous()
+    B = lam_t.numel()
+    A = torch.zeros(B, n, dtype=torch.float64, device=dev) if alpha0 is None else \
+        alpha0.reshape(B, n).to(torch.float64).clone().contiguous()
+    yd = y.to(dev, torch.float64).contiguous()
+    mk = None if mask is None else mask.reshape(B, n).to(dev, torch.uint8).contiguous()
+    prob = tk_problem(m, n, dtype_code(K.dtype), K.data_ptr(), yd.data_ptr(), B, lam_t.data_ptr(),
+                      0 if mk is None else mk.data_ptr())
+    opts = tk_solve_opts(TK_NEWTON_CG if method == "newton_cg" else TK_GD_BT, tol, max_iter, max_cg, 0.0)
+    need = int(lib().tk_solve_workspace_size(ctypes.byref(prob)))
+    if need == 0:
+        raise TKError(TK_EINVAL, lib().tk_last_error().decode())
+    key = dev.index
+    ws = _solve_ws.get(key)
+    if ws is None or ws.numel() < need:
+        ws = torch.zeros(need, dtype=torch.uint8, device=dev)
+        _solve_ws[key] = ws
+    reps = (tk_solve_report * B)()
+    rc = lib().tk_solve_dual(ctypes.byref(prob), ctypes.byref(opts), _p(A), reps, _p(ws), ws.numel(),
+                             _stream(stream))
+    if rc not in (TK_OK, TK_ENOTCONV):
+        _check(rc)
+    out = [{f: getattr(r, f) for f, _ in r._fields_} for r in reps]
+    return A, out, rc
