@@ -28,8 +28,9 @@
  *     stream).  Device calls are asynchronous on that stream unless noted.
  *   - Device buffers must be 16-byte aligned (every cudaMalloc / PyTorch
  *     allocation is).
- *   - Results are deterministic: no floating-point atomics; every reduction
- *     runs in a fixed order.
+ *   - No floating-point atomics; every reduction runs in a fixed order, and
+ *     with the default schedule (tk_contract_config.schedule) results are
+ *     bit-reproducible from run to run.
  */
 #ifndef TK_H
 #define TK_H
@@ -158,8 +159,12 @@ int tk_contract_range(int m, int64_t n, int storage_dtype, const void *K_range,
  *   ctas_per_sm  blocks per SM (1 or 2)
  *   row_cost     cost of one row, in entries, when the range is cut into pieces
  *   tri_cost     cost of entering a triangle (prefix i_1..i_{m-2}), in entries
- *   pieces_per_warp  the range is cut into this many pieces per warp, which
- *                warps take from a shared counter as they finish (1..16) */
+ *   pieces_per_warp  the range is cut into this many pieces per warp (1..16)
+ *   schedule     1: warp w takes pieces w, w+W, w+2W, ... (W warps; results are
+ *                bit-reproducible); 2: warps take the next free piece from a
+ *                shared counter as they finish (balances better; the order in
+ *                which partial sums meet varies, so results vary in the last
+ *                bits).  0 = library choice (1). */
 typedef struct {
     int warps;
     int block_log2;
@@ -168,6 +173,7 @@ typedef struct {
     int row_cost;
     int tri_cost;
     int pieces_per_warp;
+    int schedule;
 } tk_contract_config;
 
 /* Sets the process-wide contraction configuration (NULL restores the
@@ -235,6 +241,28 @@ int tk_objective(int m, int64_t n, int storage_dtype, const void *K, int64_t B,
 int tk_assemble_objective(int m, int64_t n, int64_t B, const double *G, const double *S, const double *A,
                           const double *y, const double *lambda, double *F, double *grad, double *gnorm,
                           void *stream);
+
+/* ------------------------------------------------------------ primal side */
+
+/* Representer map of Section 4 (eq. tensor_representer) for the linear tensor
+ * kernel: w_b = J_q(X^T a_b) with q = m, i.e. w_k = sign(u_k)|u_k|^{m-1},
+ * u = X^T a_b (= u_k^{m-1} for even m).  X: n x d row-major, A: B x n,
+ * W: B x d; FP64 device pointers. */
+int tk_primal(int m, int64_t n, int64_t d, const double *X, int64_t B, const double *A, double *W, void *stream);
+
+/* Test-phase estimate of Section 4 (eq. tensor_1) with the linear kernel:
+ * Yhat[b][j] = <w_b, x_j> for the t rows of Xtest (t x d row-major).
+ * W: B x d, Yhat: B x t; FP64 device pointers. */
+int tk_predict(int64_t t, int64_t d, const double *Xtest, int64_t B, const double *W, double *Yhat, void *stream);
+
+/* Nystrom-like subsampling of Section 6.1: n_prime of the N training indices,
+ * uniform without replacement, sorted ascending, written to idx_host (host).
+ * Generator (so that any implementation reproduces the same indices):
+ * SplitMix64 (Steele, Lea and Flood 2014) seeded with `seed`; for
+ * j = N - n_prime .. N-1, draw x until x < (2^64 - 1) - ((2^64 - 1) mod (j + 1)),
+ * r = x mod (j + 1), and take r unless it was taken already, else take j
+ * (Floyd's algorithm, Bentley and Floyd 1987).  Host only. */
+int tk_nystrom_select(int64_t N, int64_t n_prime, uint64_t seed, int64_t *idx_host);
 
 /* ------------------------------------------------------------ dual solver */
 

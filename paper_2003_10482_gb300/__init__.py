@@ -79,6 +79,9 @@ def _declare(L):
         "tk_assemble_objective": (i32, [i32, i64, i64, P, P, P, P, P, P, P, P, P]),
         "tk_contract_noalloc": (i32, [i32, i64, i32, P, i32, P, P, P, P]),
         "tk_solve_workspace_size": (sz, [P]),
+        "tk_primal": (i32, [i32, i64, i64, P, i64, P, P, P]),
+        "tk_predict": (i32, [i64, i64, P, i64, P, P, P]),
+        "tk_nystrom_select": (i32, [i64, i64, u64, P]),
         "tk_solve_dual": (i32, [P, P, P, P, P, sz, P]),
     }
     for name, (res, args) in sig.items():
@@ -179,21 +182,21 @@ def workspace(m: int, n: int, B: int = 1, device=None) -> torch.Tensor:
 class tk_contract_config(ctypes.Structure):
     _fields_ = [("warps", ctypes.c_int), ("block_log2", ctypes.c_int), ("nbuf", ctypes.c_int),
                 ("ctas_per_sm", ctypes.c_int), ("row_cost", ctypes.c_int), ("tri_cost", ctypes.c_int),
-                ("pieces_per_warp", ctypes.c_int)]
+                ("pieces_per_warp", ctypes.c_int), ("schedule", ctypes.c_int)]
 
 
 def tk_contract_set_config(warps=0, block_log2=0, nbuf=0, ctas_per_sm=0, row_cost=0, tri_cost=0,
-                           pieces_per_warp=0, reset=False):
+                           pieces_per_warp=0, schedule=0, reset=False):
     """Process-wide launch configuration of the contraction (0 = library choice)."""
     if reset:
         _check(lib().tk_contract_set_config(None))
         return
-    c = tk_contract_config(warps, block_log2, nbuf, ctas_per_sm, row_cost, tri_cost, pieces_per_warp)
+    c = tk_contract_config(warps, block_log2, nbuf, ctas_per_sm, row_cost, tri_cost, pieces_per_warp, schedule)
     _check(lib().tk_contract_set_config(ctypes.byref(c)))
 
 
-def tk_contract_plan(m: int, n: int, off_lo: int, off_hi: int, pieces: int, row_cost: int = 48,
-                     tri_cost: int = 192) -> list[int]:
+def tk_contract_plan(m: int, n: int, off_lo: int, off_hi: int, pieces: int, row_cost: int = 256,
+                     tri_cost: int = 1024) -> list[int]:
     """Row-aligned cut of [off_lo, off_hi) into `pieces` near-equal-cost pieces (host only)."""
     out = (ctypes.c_int64 * (pieces + 1))()
     _check(lib().tk_contract_plan(m, n, off_lo, off_hi, pieces, row_cost, tri_cost, out))
@@ -365,3 +368,37 @@ def tk_solve_dual(K: torch.Tensor, m: int, n: int, y: torch.Tensor, lam, alpha0:
         _check(rc)
     out = [{f: getattr(r, f) for f, _ in r._fields_} for r in reps]
     return A, out, rc
+
+
+def tk_primal(X: torch.Tensor, A: torch.Tensor, m: int, stream=None) -> torch.Tensor:
+    """w = J_q(X^T a) for each row of A (linear tensor kernel), FP64 (B x d)."""
+    X = X.to(torch.float64).contiguous()
+    n, d = X.shape
+    A2 = A.reshape(-1, n).to(torch.float64).contiguous()
+    W = torch.empty(A2.shape[0], d, dtype=torch.float64, device=X.device)
+    _check(lib().tk_primal(m, n, d, _p(X), A2.shape[0], _p(A2), _p(W), _stream(stream)))
+    return W if A.dim() > 1 else W.reshape(d)
+
+
+def tk_predict(Xtest: torch.Tensor, W: torch.Tensor, stream=None) -> torch.Tensor:
+    """<w_b, x_j> for every test row (B x t, FP64)."""
+    Xt = Xtest.to(torch.float64).contiguous()
+    t, d = Xt.shape
+    W2 = W.reshape(-1, d).to(torch.float64).contiguous()
+    Y = torch.empty(W2.shape[0], t, dtype=torch.float64, device=Xt.device)
+    _check(lib().tk_predict(t, d, _p(Xt), W2.shape[0], _p(W2), _p(Y), _stream(stream)))
+    return Y if W.dim() > 1 else Y.reshape(t)
+
+
+def tk_nystrom_select(N: int, n_prime: int, seed: int) -> list[int]:
+    """n' of N indices, uniform without replacement, sorted (host, Section 6.1)."""
+    out = (ctypes.c_int64 * max(n_prime, 1))()
+    _check(lib().tk_nystrom_select(N, n_prime, ctypes.c_uint64(seed & (2**64 - 1)), out))
+    return list(out)[:n_prime]
+
+
+def support_threshold(w) -> list[int]:
+    """Features with |w_j| > 2 std(w) (the adaptive threshold of Section 6.3); host."""
+    import numpy as np
+    w = np.asarray(w.detach().cpu() if hasattr(w, "detach") else w, dtype=np.float64)
+    return list(np.nonzero(np.abs(w) > 2.0 * np.std(w))[0])

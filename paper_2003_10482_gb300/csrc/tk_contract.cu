@@ -81,7 +81,7 @@ static int pick_nc(int n) {
 }
 
 
-tk_contract_config g_contract_cfg = {0, 0, 0, 0, 0, 0, 0};
+tk_contract_config g_contract_cfg = {0, 0, 0, 0, 0, 0, 0, 0};
 
 static const int kMaxWarps = 16;
 
@@ -211,7 +211,8 @@ static int ensure_plan(const PlanKey &key, void *plan_region, cudaStream_t st) {
 
 // ------------------------------------------------------------------ launch config
 struct Resolved {
-  int nc, warps, nbuf, buf_bytes, cap, vec_bytes, warp_bytes, grid, cps, row_cost, tri_cost, block_log2, ppw;
+  int nc, warps, nbuf, buf_bytes, cap, vec_bytes, warp_bytes, grid, cps, row_cost, tri_cost, block_log2, ppw,
+      schedule;
   size_t smem;
 };
 
@@ -251,10 +252,12 @@ static int resolve(int m, int n, int storage, bool dual, Resolved *r) {
   r->warps = warps;
   r->grid = di.sms * r->cps;
   r->smem = (size_t)r->vec_bytes + (size_t)warps * r->warp_bytes;
-  r->row_cost = o.row_cost > 0 ? o.row_cost : 1024;
+  r->row_cost = o.row_cost > 0 ? o.row_cost : 256;
   r->tri_cost = o.tri_cost > 0 ? o.tri_cost : 4 * r->row_cost;
   r->ppw = o.pieces_per_warp > 0 ? o.pieces_per_warp : 16;
   if (r->ppw > kMaxPiecesPerWarp) return fail(TK_EINVAL, "pieces_per_warp above %d", kMaxPiecesPerWarp);
+  r->schedule = o.schedule > 0 ? o.schedule : 1;
+  if (r->schedule > 2) return fail(TK_EINVAL, "schedule must be 1 or 2");
   return TK_OK;
 }
 
@@ -269,6 +272,7 @@ int contract_resolve(int m, int n, int storage, bool dual, tk_contract_config *o
   out->row_cost = r.row_cost;
   out->tri_cost = r.tri_cost;
   out->pieces_per_warp = r.ppw;
+  out->schedule = r.schedule;
   if (grid) *grid = r.grid;
   return TK_OK;
 }
@@ -305,6 +309,7 @@ int contract_pass(const ContractArgs &a, int *grid_out, const double **part_out,
   kp.pieces = pieces;
   kp.ticket = &hdr->ticket;
   kp.done = &hdr->done;
+  kp.dynamic = r.schedule == 2;
   kp.fin = a.fin;
   kp.fin.part = part;
   kp.fin.grid = r.grid;
@@ -364,6 +369,7 @@ int contract_pass_static(const ContractArgs &a, WarpPlan *host_plan, int host_ca
   kp.pieces = pieces;
   kp.ticket = &hdr->ticket;
   kp.done = &hdr->done;
+  kp.dynamic = r.schedule == 2;
   kp.fin = a.fin;
   kp.fin.part = part;
   kp.fin.grid = r.grid;

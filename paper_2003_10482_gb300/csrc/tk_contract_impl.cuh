@@ -202,6 +202,7 @@ struct KParams {
   int pieces;
   unsigned long long *ticket;  // next piece to hand out (zeroed before the launch)
   unsigned int *done;          // blocks finished (zeroed before the launch)
+  int dynamic;                 // 1: shared-ticket schedule, 0: warp w takes w, w+W, ...
   FinalizeArgs fin;            // outputs the last block writes
   int warps;
   int nbuf;         // linear staging buffers per warp
@@ -411,7 +412,15 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
   // copy side of a warp takes the next piece when it has issued every block
   // of the current one, and tags each block with its piece so that the
   // compute side switches in step.
+  const int W = (int)gridDim.x * p.warps;
+  const int wg = (int)blockIdx.x * p.warps + wid;
+  int next_static = wg;
   auto grab = [&]() -> int {
+    if (!p.dynamic) {
+      const int t = next_static;
+      next_static += W;
+      return t < p.pieces ? t : -1;
+    }
     unsigned long long t = 0;
     if (lane == 0) t = atomicAdd(p.ticket, 1ull);
     t = __shfl_sync(0xffffffffu, t, 0);

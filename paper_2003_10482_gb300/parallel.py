@@ -15,7 +15,7 @@ import torch.distributed as dist
 import paper_2003_10482_gb300 as tk
 
 
-def shard_bounds(m: int, n: int, world: int, row_cost: int = 1024, tri_cost: int = 4096) -> list[int]:
+def shard_bounds(m: int, n: int, world: int, row_cost: int = 256, tri_cost: int = 1024) -> list[int]:
     """world+1 row-aligned offsets cutting [0, N) into near-equal-cost shards."""
     N = tk.tk_packed_size(m, n)
     return tk.tk_contract_plan(m, n, 0, N, world, row_cost, tri_cost)

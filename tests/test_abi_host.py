@@ -107,3 +107,14 @@ def test_contract_plan_is_row_aligned_and_balanced(L, m, n, pieces):
         for x, y in zip(b[:-1], b[1:]):
             piece = sum(c for o, c in rows if x <= o < y)
             assert piece <= total / pieces + big + tc
+
+
+@pytest.mark.parametrize("N,np_,seed", [(50_000, 600, 2003_10485), (20_000, 300, 2003_10486), (7, 3, 1),
+                                        (10, 10, 5), (10, 0, 5), (1, 1, 0), (1000, 999, 2**63 + 7)])
+def test_nystrom_select_matches_oracle(L, N, np_, seed):
+    assert tk.tk_nystrom_select(N, np_, seed) == list(oracle.nystrom_select(N, np_, seed))
+
+
+def test_nystrom_select_rejects_bad_sizes(L):
+    with pytest.raises(tk.TKError):
+        tk.tk_nystrom_select(5, 6, 1)
