@@ -129,11 +129,12 @@ int tk_row_align(int m, int64_t n, int64_t off, int64_t *row_off) {
 }
 
 size_t tk_contract_workspace_size(int m, int64_t n, int64_t B) {
-  (void)B;
   if (check_order_points(m, n) != TK_OK) return 0;
   DevInfo di;
   if (dev_info(&di) != TK_OK) return 0;
-  return contract_workspace_bytes((int)n, di.sms);
+  size_t need = contract_workspace_bytes((int)n, di.sms);
+  if (B > 1) need = std::max(need, batched_workspace_bytes((int)n, B, di.sms));
+  return need;
 }
 
 static int contract_impl(int m, int64_t n, int storage, const void *K, int64_t off_lo, int64_t off_hi,
@@ -159,10 +160,32 @@ static int contract_impl(int m, int64_t n, int storage, const void *K, int64_t o
   if (rc != TK_OK) return rc;
   const size_t need = contract_workspace_bytes((int)n, di.sms);
   if (work_bytes < need) return fail(TK_ENOMEM, "workspace %zu < %zu bytes", work_bytes, need);
+  const bool use_batched_ws = B > 1 && work_bytes >= batched_workspace_bytes((int)n, B, di.sms);
+  (void)use_batched_ws;
 
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int vs = vec_dtype == TK_F64 ? 8 : 4;
   unsigned char *wsb = reinterpret_cast<unsigned char *>(work);
+  if (B > 1 && storage != TK_F64) {
+    // one pass for the whole batch when the batched kernel covers the shape
+    BatchedArgs ba;
+    ba.m = m;
+    ba.n = (int)n;
+    ba.storage = storage;
+    ba.K = K;
+    ba.off_lo = off_lo;
+    ba.off_hi = off_hi;
+    ba.B = B;
+    ba.vec_dtype = vec_dtype;
+    ba.A = A;
+    ba.V = (r == m - 2) ? V : nullptr;
+    ba.G = G;
+    ba.S = (r == m - 1) ? S : nullptr;
+    ba.work = work;
+    ba.work_bytes = work_bytes;
+    rc = contract_batched(ba, st);
+    if (rc != TK_EUNSUPPORTED) return rc;
+  }
   for (int64_t b = 0; b < B; ++b) {
     ContractArgs a;
     memset(&a, 0, sizeof(a));

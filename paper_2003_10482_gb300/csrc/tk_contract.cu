@@ -209,6 +209,12 @@ static int ensure_plan(const PlanKey &key, void *plan_region, cudaStream_t st) {
   return TK_OK;
 }
 
+int plan_to_device(int m, int n, int64_t lo, int64_t hi, int pieces, int row_cost, int tri_cost, void *region,
+                   cudaStream_t st) {
+  PlanKey key{m, n, lo, hi, pieces, row_cost, tri_cost};
+  return ensure_plan(key, region, st);
+}
+
 // ------------------------------------------------------------------ launch config
 struct Resolved {
   int nc, warps, nbuf, buf_bytes, cap, vec_bytes, warp_bytes, grid, cps, row_cost, tri_cost, block_log2, ppw,

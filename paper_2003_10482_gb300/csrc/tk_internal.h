@@ -43,6 +43,28 @@ static_assert(sizeof(WarpPlan) == 48, "plan record");
 void build_plan(int m, int n, int64_t lo, int64_t hi, int pieces, int64_t row_cost, int64_t tri_cost,
                 WarpPlan *out);
 
+// Upload (once, cached per region) the cut of [lo, hi) into `pieces` pieces.
+int plan_to_device(int m, int n, int64_t lo, int64_t hi, int pieces, int row_cost, int tri_cost, void *region,
+                   cudaStream_t st);
+
+// Batched contraction (one pass for B vectors); returns TK_EUNSUPPORTED when
+// the shape is outside what the batched kernel covers (callers then loop).
+struct BatchedArgs {
+  int m, n, storage;
+  const void *K;
+  int64_t off_lo, off_hi;
+  int64_t B;
+  int vec_dtype;
+  const void *A;   // B x n
+  const void *V;   // B x n or NULL (dual pass)
+  void *G;         // B x n, vec_dtype (r = m-1: K[a^{m-1}]; dual: K[a^{m-2}, v])
+  double *S;       // B or NULL (r = m-1 only)
+  void *work;
+  size_t work_bytes;
+};
+int contract_batched(const BatchedArgs &a, cudaStream_t st);
+size_t batched_workspace_bytes(int n, int64_t B, int sms);
+
 // Device properties cached per device.
 struct DevInfo {
   int sms;
