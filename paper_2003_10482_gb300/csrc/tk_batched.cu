@@ -218,7 +218,11 @@ __global__ void __launch_bounds__(kBT, 1) batched_kernel(BParams p) {
   bool prod_done = piece_p < 0;
   int piece_c = -1;
   const int64_t tail_lo = p.bytes & ~int64_t(15);
-  int64_t j_issue = 0, j_cons = 0;
+  // blocks issued / consumed; buffer index and mbarrier phase of each side
+  // advance with wrap-around (no division by the runtime buffer count)
+  int j_issue = 0, j_cons = 0;
+  int bi_issue = 0, bi_cons = 0;
+  uint32_t ph_cons = 0;
 
   // the copy side runs on every thread (uniform state), thread 0 issues
   auto issue_next = [&]() {
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(kBT, 1) batched_kernel(BParams p) {
     const int nb = block_rows(n, cp, posp, endp, p.cap);
     const int L0 = n - cp;
     const int64_t pend = posp + (int64_t)(nb * L0 - (nb * (nb - 1)) / 2);
-    const int bi = (int)(j_issue % NB);
+    const int bi = bi_issue;
     const int64_t b0 = ((posp - p.off_lo) * ES) & ~int64_t(15);
     const int64_t b1 = min((((pend - p.off_lo) * ES) + 15) & ~int64_t(15), tail_lo);
     if (threadIdx.x == 0) {
@@ -256,6 +260,7 @@ __global__ void __launch_bounds__(kBT, 1) batched_kernel(BParams p) {
       if (m > 2 && next_sorted(m - 2, n, Qp)) cp = Qp[m - 3];
     }
     ++j_issue;
+    bi_issue = (bi_issue + 1 == NB) ? 0 : bi_issue + 1;
   };
 
   // ------------------------------------------------------------ triangle state (per vector)
@@ -358,8 +363,8 @@ __global__ void __launch_bounds__(kBT, 1) batched_kernel(BParams p) {
   int rows_since_flush = 0;
 
   while (j_cons < j_issue) {
-    const int bi = (int)(j_cons % NB);
-    const uint32_t parity = (uint32_t)((j_cons / NB) & 1);
+    const int bi = bi_cons;
+    const uint32_t parity = ph_cons;
     const int nb = desc_nb[bi];
     const int piece = desc_pc[bi];
     if (piece != piece_c) {
@@ -396,6 +401,10 @@ __global__ void __launch_bounds__(kBT, 1) batched_kernel(BParams p) {
       }
     }
     ++j_cons;
+    if (++bi_cons == NB) {
+      bi_cons = 0;
+      ph_cons ^= 1u;
+    }
     __syncthreads();  // tail bytes visible; the previous block's buffer is free
     issue_next();
 

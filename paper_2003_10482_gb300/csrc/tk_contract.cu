@@ -243,7 +243,8 @@ static int resolve(int m, int n, int storage, bool dual, Resolved *r) {
   const int fixed = cts == 8 ? (dual ? warp_fixed_bytes<double, true>() : warp_fixed_bytes<double, false>())
                               : (dual ? warp_fixed_bytes<float, true>() : warp_fixed_bytes<float, false>());
   const int gbytes = ((dual ? 2 : 1) * n * cts + 127) & ~127;
-  r->vec_bytes = ((dual ? 2 : 1) * n * cts + 127) & ~127;
+  // staged vectors, then the rows-fit table (n+1 shorts) at the end of the region
+  r->vec_bytes = ((dual ? 2 : 1) * n * cts + 2 * (n + 1) + 2 + 127) & ~127;
   r->warp_bytes = fixed + gbytes + r->nbuf * r->buf_bytes;
   r->warp_bytes = (r->warp_bytes + 127) & ~127;
   r->cps = o.ctas_per_sm > 0 ? o.ctas_per_sm : 1;

@@ -227,11 +227,14 @@ constexpr int max_threads() {
 // of each issued block.
 struct WarpHdr {
   uint64_t bar[8];
-  int nb[8];
-  int piece[8];
+  int nb[8];      // rows of the block
+  int piece[8];   // piece it belongs to
+  int boff[8];    // element offset of its first entry in the buffer
+  int flags[8];   // bit 0: a bulk copy was issued; bits 8..: tail bytes to copy by hand
+  int tdst[8];    // buffer byte offset of the tail bytes
   int pad[8];
 };
-static_assert(sizeof(WarpHdr) == 160, "warp header");
+static_assert(sizeof(WarpHdr) == 256, "warp header");
 
 // Per-row data of the current block, written by lane i for row i and read
 // back by the whole warp with one broadcast load.
@@ -245,7 +248,7 @@ struct __align__(16) RowInfo {
 template <typename CT, bool D>
 __host__ __device__ constexpr int warp_fixed_bytes() {
   // header, row info, dot tile(s); 128-byte aligned
-  return ((160 + kRB * (int)sizeof(RowInfo<CT>) + (D ? 2 : 1) * kDsmLen * (int)sizeof(CT)) + 127) & ~127;
+  return ((256 + kRB * (int)sizeof(RowInfo<CT>) + (D ? 2 : 1) * kDsmLen * (int)sizeof(CT)) + 127) & ~127;
 }
 
 // rows of the block that starts at row c (position pos) of its triangle:
@@ -382,8 +385,8 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
   CT *v_s = a_s + n;
   unsigned char *wb = smem + p.vec_bytes + (size_t)wid * p.warp_bytes;
   WarpHdr *hdr = reinterpret_cast<WarpHdr *>(wb);
-  RowInfo<CT> *rinfo = reinterpret_cast<RowInfo<CT> *>(wb + 160);
-  CT *dsm_v = reinterpret_cast<CT *>(wb + 160 + kRB * sizeof(RowInfo<CT>));
+  RowInfo<CT> *rinfo = reinterpret_cast<RowInfo<CT> *>(wb + 256);
+  CT *dsm_v = reinterpret_cast<CT *>(wb + 256 + kRB * sizeof(RowInfo<CT>));
   CT *dsm_d = dsm_v + kDsmLen;
   CT *g_v = reinterpret_cast<CT *>(wb + warp_fixed_bytes<CT, D>());
   CT *g_d = g_v + n;
@@ -391,9 +394,17 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
   unsigned char *bufs = wb + warp_fixed_bytes<CT, D>() + gbytes;
   const int NB = p.nbuf;
 
+  // rows of a block that starts with a row of length L (rows shrink by one):
+  // at most kRB, at most L, within `cap` entries
+  short *rfit = reinterpret_cast<short *>(smem + p.vec_bytes - 2 * (n + 1) - 2);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     a_s[i] = ld_vec<CT>(p.alpha, p.vec_dtype, i);
     if (D) v_s[i] = ld_vec<CT>(p.v, p.vec_dtype, i);
+  }
+  for (int L = threadIdx.x; L <= n; L += blockDim.x) {
+    int r = min(kRB, L);
+    while (r > 1 && r * L - (r * (r - 1)) / 2 > p.cap) --r;
+    rfit[L] = (short)max(r, 1);
   }
   for (int i = lane; i < n; i += 32) {
     g_v[i] = CT(0);
@@ -441,7 +452,11 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
   int piece_c = -1;
 
   const int64_t tail_lo = p.bytes & ~int64_t(15);
-  int64_t j_issue = 0, j_cons = 0;
+  // blocks issued / consumed; buffer index and mbarrier phase of each side
+  // advance with wrap-around (no division by the runtime buffer count)
+  int j_issue = 0, j_cons = 0;
+  int bi_issue = 0, bi_cons = 0;
+  uint32_t ph_cons = 0;
   bool failed = false;
 
   // issue the bulk copy of the next block at the copy cursor
@@ -459,15 +474,26 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
       endp = pl.end;
     }
     if (prod_done) return;
-    const int nb = block_rows(n, cp, posp, endp, p.cap);
     const int L0 = n - cp;
-    const int64_t pend = posp + (int64_t)(nb * L0 - (nb * (nb - 1)) / 2);
-    const int bi = (int)(j_issue % NB);
-    const int64_t b0 = ((posp - p.off_lo) * ES) & ~int64_t(15);
-    const int64_t b1 = min((((pend - p.off_lo) * ES) + 15) & ~int64_t(15), tail_lo);
+    int nb = rfit[L0];
+    int span = nb * L0 - (nb * (nb - 1)) / 2;
+    while (nb > 1 && posp + span > endp) {  // the piece ends inside this block (rare)
+      --nb;
+      span -= L0 - nb;
+    }
+    const int64_t pend = posp + span;
+    const int bi = bi_issue;
+    const int64_t rb0 = (posp - p.off_lo) * ES;
+    const int64_t b0 = rb0 & ~int64_t(15);
+    const int64_t rb1 = (pend - p.off_lo) * ES;
+    const int64_t b1 = min((rb1 + 15) & ~int64_t(15), tail_lo);
     if (lane == 0) {
       hdr->nb[bi] = nb;
       hdr->piece[bi] = piece_p;
+      hdr->boff[bi] = (int)(rb0 - b0) / ES;
+      const int tail = rb1 > tail_lo ? (int)(rb1 - max(tail_lo, b0)) : 0;
+      hdr->flags[bi] = (b1 > b0 ? 1 : 0) | (tail << 8);
+      hdr->tdst[bi] = (int)(max(tail_lo, b0) - b0);
       if (b1 > b0) {
         fence_proxy_async();
         mbar_expect_tx(&hdr->bar[bi], (uint32_t)(b1 - b0));
@@ -480,6 +506,7 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
       if (m > 2 && next_sorted(m - 2, n, Qp)) cp = Qp[m - 3];
     }
     ++j_issue;
+    bi_issue = (bi_issue + 1 == NB) ? 0 : bi_issue + 1;
   };
 
   // ------------------------------------------------------------ accumulators
@@ -567,8 +594,8 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
 
   while (j_cons < j_issue && !failed) {
     // ---------------------------------------------------- wait for this block
-    const int bi = (int)(j_cons % NB);
-    const uint32_t parity = (uint32_t)((j_cons / NB) & 1);
+    const int bi = bi_cons;
+    const uint32_t parity = ph_cons;
     __syncwarp();
     const int nb = hdr->nb[bi];
     const int piece = hdr->piece[bi];
@@ -586,12 +613,9 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
     }
     const int L0 = n - c;
     const int64_t pend = pos + (int64_t)(nb * L0 - (nb * (nb - 1)) / 2);
-    const int64_t rb0 = (pos - p.off_lo) * ES;
-    const int64_t b0 = rb0 & ~int64_t(15);
-    const int64_t rb1 = (pend - p.off_lo) * ES;
-    const int64_t b1 = min((rb1 + 15) & ~int64_t(15), tail_lo);
+    const int flags = hdr->flags[bi];
     unsigned char *buf = bufs + (size_t)bi * p.buf_bytes;
-    if (b1 > b0) {
+    if (flags & 1) {
       const bool ok = mbar_wait_bounded(&hdr->bar[bi], parity);
       if (!__all_sync(0xffffffffu, ok)) {
         if (lane == 0) {
@@ -602,21 +626,23 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
         break;
       }
     }
-    if (rb1 > tail_lo) {
+    if (flags >> 8) {
       // bytes past the last 16-byte boundary of the array: plain loads
-      const int64_t nt = rb1 - max(tail_lo, b0);
-      if (lane < nt) {
-        const int64_t src = max(tail_lo, b0) + lane;
-        buf[src - b0] = p.K[src];
-      }
+      const int nt = flags >> 8, dst = hdr->tdst[bi];
+      if (lane < nt) buf[dst + lane] = p.K[tail_lo + lane];
     }
+    const int boff = hdr->boff[bi];
     ++j_cons;
+    if (++bi_cons == NB) {
+      bi_cons = 0;
+      ph_cons ^= 1u;
+    }
     __syncwarp();
     // the previous block's buffer is free again: keep NBUF-1 copies in flight
     issue_next();
 
     // ---------------------------------------------------- rows of the block
-    const ST *bp = reinterpret_cast<const ST *>(buf) + (int)((rb0 - b0) / ES);
+    const ST *bp = reinterpret_cast<const ST *>(buf) + boff;
     if (lane < kRB) {
       // row data, one lane per row
       const int i = lane;
@@ -779,9 +805,12 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
   if (open) flush_triangle();
   // drain copies still in flight before the block can exit
   while (j_cons < j_issue) {
-    const int bi = (int)(j_cons % NB);
-    mbar_wait_bounded(&hdr->bar[bi], (uint32_t)((j_cons / NB) & 1));
+    mbar_wait_bounded(&hdr->bar[bi_cons], ph_cons);
     ++j_cons;
+    if (++bi_cons == NB) {
+      bi_cons = 0;
+      ph_cons ^= 1u;
+    }
   }
   __syncwarp();
 
