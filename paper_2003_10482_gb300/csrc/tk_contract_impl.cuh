@@ -761,13 +761,18 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
     // ---------------------------------------------------- row dots and epilogue
     {
       const int r = lane & 15, h = lane >> 4;
-      N s = mk<CT, D>(CT(0), CT(0));
+      // sixteen partials in registers, then a pairwise tree (short dependence chain)
+      N t[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int a = dsm_index(16 * h + i, r);
-        s.v += dsm_v[a];
-        if (D) s.d += dsm_d[a];
+        t[i] = mk<CT, D>(dsm_v[a], D ? dsm_d[a] : CT(0));
       }
+#pragma unroll
+      for (int w2 = 8; w2 >= 1; w2 >>= 1)
+#pragma unroll
+        for (int i = 0; i < w2; ++i) t[i] = t[i] + t[i + w2];
+      N s = t[0];
       s = s + shfl_xor(s, 16);
       if (h == 0 && r < nb) {
         const int ci = c + r;
