@@ -130,6 +130,13 @@ __device__ __forceinline__ Nm<T, D> shfl_xor(Nm<T, D> a, int mask) {
   return r;
 }
 template <typename T, bool D>
+__device__ __forceinline__ Nm<T, D> shfl_idx(Nm<T, D> a, int src) {
+  Nm<T, D> r;
+  r.v = __shfl_sync(0xffffffffu, a.v, src);
+  r.d = D ? __shfl_sync(0xffffffffu, a.d, src) : T(0);
+  return r;
+}
+template <typename T, bool D>
 __device__ __forceinline__ Nm<T, D> sel(bool c, Nm<T, D> a, Nm<T, D> b) {
   return c ? a : b;
 }
@@ -223,16 +230,17 @@ constexpr int max_threads() {
   return max_threads_est((int)sizeof(CT), D, NC);
 }
 
-// Per-warp shared-memory header: NBUF mbarriers and the row count and piece
-// of each issued block.
+// Per-warp shared-memory header: NBUF mbarriers and the descriptor of each
+// issued block: {piece, nb | boff << 5 | BULK | TAIL | LAST}.
+constexpr int kDescBulk = 1 << 9;   // a bulk copy was issued for the block
+constexpr int kDescTail = 1 << 10;  // its last bytes (past the array's last 16-byte boundary) are copied by hand
+constexpr int kDescLast = 1 << 11;  // the last block of its piece
 struct WarpHdr {
   uint64_t bar[8];
-  int nb[8];      // rows of the block
-  int piece[8];   // piece it belongs to
-  int boff[8];    // element offset of its first entry in the buffer
-  int flags[8];   // bit 0: a bulk copy was issued; bits 8..: tail bytes to copy by hand
-  int tdst[8];    // buffer byte offset of the tail bytes
-  int pad[8];
+  int2 desc[8];
+  int tcut[8];    // buffer byte offset of the hand-copied tail
+  int tlen[8];    // tail bytes
+  int pad[16];
 };
 static_assert(sizeof(WarpHdr) == 256, "warp header");
 
@@ -262,22 +270,34 @@ __device__ __forceinline__ int block_rows(int n, int c, int64_t pos, int64_t end
   return r;
 }
 
-// One 32-column chunk of four consecutive rows: lane j takes, in each row i,
-// the entry of column d = n-1-(32K+j), adds it into g_d's accumulator and into
-// row i's dot.  MASK: the chunk may run past the end of a row.
-template <int K, bool MASK, int NC, typename ST, typename CT, bool D>
-__device__ __forceinline__ void quad_chunk(Nm<CT, D> (&acc)[NC], Nm<CT, D> (&dot)[4], const Nm<CT, D> (&ar)[NC],
-                                           const ST *const (&prow)[4], const int (&sl)[4], int lane,
-                                           const Nm<CT, D> (&cf)[4]) {
+// One 32-column chunk K of four consecutive rows, software-pipelined: lane j
+// holds, in xc[i], the entry of row i at column d = n-1-(32K+j) (loaded one
+// step earlier), adds it into g_d's accumulator and into row i's dot; before
+// that it issues the loads of chunk K-1 into xn[] (zero past a row's end when
+// MASKN, so the multiply-adds need no masks).
+template <int K, bool MASKN, int NC, typename ST, typename CT, bool D>
+__device__ __forceinline__ void quad_step(Nm<CT, D> (&acc)[NC], Nm<CT, D> (&dot)[4], const Nm<CT, D> (&ar)[NC],
+                                          const ST *const (&prow)[4], const int (&sl)[4], int lane,
+                                          const Nm<CT, D> (&cf)[4], const CT (&xc)[4], CT (&xn)[4]) {
+  if constexpr (K >= 1 && K - 1 < NC) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      xn[i] = (!MASKN || 32 * (K - 1) + lane < sl[i]) ? ld_elem<ST, CT>(prow[i] - 32 * (K - 1)) : CT(0);
+  }
   if constexpr (K < NC) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      if (!MASK || 32 * K + lane < sl[i]) {
-        const CT x = ld_elem<ST, CT>(prow[i] - 32 * K);
-        fma_acc(acc[K], x, cf[i]);
-        fma_acc(dot[i], x, ar[K]);
-      }
+      fma_acc(acc[K], xc[i], cf[i]);
+      fma_acc(dot[i], xc[i], ar[K]);
     }
+  }
+}
+// masked loads of the top chunk K of a quad
+template <int K, int NC, typename ST, typename CT>
+__device__ __forceinline__ void quad_load(const ST *const (&prow)[4], const int (&sl)[4], int lane, CT (&x)[4]) {
+  if constexpr (K < NC) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x[i] = (32 * K + lane < sl[i]) ? ld_elem<ST, CT>(prow[i] - 32 * K) : CT(0);
   }
 }
 
@@ -419,10 +439,11 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
   auto alpha_at = [&](int i) -> N { return mk<CT, D>(a_s[i], D ? v_s[i] : CT(0)); };
 
   // ------------------------------------------------------------ pieces
-  // Warps take cost-balanced pieces of the range from a shared ticket: the
-  // copy side of a warp takes the next piece when it has issued every block
-  // of the current one, and tags each block with its piece so that the
-  // compute side switches in step.
+  // Warps take cost-balanced pieces of the range (statically, warp w taking
+  // pieces w, w+W, ..., or from a shared ticket).  The copy side of a warp
+  // takes the next piece when it has issued every block of the current one
+  // and tags each block with a descriptor; the compute side follows the
+  // descriptors and never tracks positions.
   const int W = (int)gridDim.x * p.warps;
   const int wg = (int)blockIdx.x * p.warps + wid;
   int next_static = wg;
@@ -437,21 +458,15 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
     t = __shfl_sync(0xffffffffu, t, 0);
     return t < (unsigned long long)p.pieces ? (int)t : -1;
   };
-  int32_t Q[kMaxOrder], Qp[kMaxOrder];
-  int c = 0, cp = 0;
-  int64_t pos = 0, end = 0, posp = 0, endp = 0;
-  int piece_p = grab();
-  if (piece_p >= 0) {
-    const WarpPlan &pl = p.plan[piece_p];
-    for (int j = 0; j < kMaxOrder; ++j) Qp[j] = pl.t[j];
-    cp = pl.t[m - 2];
-    posp = pl.start;
-    endp = pl.end;
-  }
-  bool prod_done = piece_p < 0;
-  int piece_c = -1;
 
-  const int64_t tail_lo = p.bytes & ~int64_t(15);
+  // copy side: piece, triangle cursor (Qp, cp), address of the next entry
+  // and the entries left in the piece
+  int32_t Qp[kMaxOrder];
+  int cp = 0, piece_p = -1;
+  const unsigned char *srcp = p.K;
+  long long remp = 0;
+  bool prod_done = false;
+  const unsigned char *const tail_ptr = p.K + (p.bytes & ~int64_t(15));
   // blocks issued / consumed; buffer index and mbarrier phase of each side
   // advance with wrap-around (no division by the runtime buffer count)
   int j_issue = 0, j_cons = 0;
@@ -461,49 +476,59 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
 
   // issue the bulk copy of the next block at the copy cursor
   auto issue_next = [&]() {
-    while (!prod_done && posp >= endp) {
+    if (prod_done) return;
+    while (remp <= 0) {
       piece_p = grab();
       if (piece_p < 0) {
         prod_done = true;
         return;
       }
       const WarpPlan &pl = p.plan[piece_p];
+      remp = pl.end - pl.start;
       for (int j = 0; j < kMaxOrder; ++j) Qp[j] = pl.t[j];
       cp = pl.t[m - 2];
-      posp = pl.start;
-      endp = pl.end;
+      srcp = p.K + (pl.start - p.off_lo) * ES;
     }
-    if (prod_done) return;
     const int L0 = n - cp;
     int nb = rfit[L0];
-    int span = nb * L0 - (nb * (nb - 1)) / 2;
-    while (nb > 1 && posp + span > endp) {  // the piece ends inside this block (rare)
+    int span = nb * L0 - ((nb * (nb - 1)) >> 1);
+    while (nb > 1 && span > remp) {  // the piece ends inside this block (rare)
       --nb;
       span -= L0 - nb;
     }
-    const int64_t pend = posp + span;
+    const uint32_t lead = (uint32_t)reinterpret_cast<uintptr_t>(srcp) & 15u;
+    const unsigned char *b0 = srcp - lead;
+    const unsigned char *e1 = srcp + span * ES;
+    uint32_t bytes = (lead + (uint32_t)(span * ES) + 15u) & ~15u;
+    int desc = nb | (int)((lead / ES) << 5);
     const int bi = bi_issue;
-    const int64_t rb0 = (posp - p.off_lo) * ES;
-    const int64_t b0 = rb0 & ~int64_t(15);
-    const int64_t rb1 = (pend - p.off_lo) * ES;
-    const int64_t b1 = min((rb1 + 15) & ~int64_t(15), tail_lo);
+    if (e1 > tail_ptr) {
+      // the block reaches past the array's last 16-byte boundary: the bytes
+      // from there are copied by hand (rare: the last block of the range)
+      const unsigned char *t0 = b0 > tail_ptr ? b0 : tail_ptr;
+      bytes = (uint32_t)(t0 - b0);
+      desc |= kDescTail;
+      if (lane == 0) {
+        hdr->tcut[bi] = (int)bytes;
+        hdr->tlen[bi] = (int)(e1 - t0);
+      }
+    }
+    if (bytes) desc |= kDescBulk;
+    remp -= span;
+    if (remp <= 0) desc |= kDescLast;
     if (lane == 0) {
-      hdr->nb[bi] = nb;
-      hdr->piece[bi] = piece_p;
-      hdr->boff[bi] = (int)(rb0 - b0) / ES;
-      const int tail = rb1 > tail_lo ? (int)(rb1 - max(tail_lo, b0)) : 0;
-      hdr->flags[bi] = (b1 > b0 ? 1 : 0) | (tail << 8);
-      hdr->tdst[bi] = (int)(max(tail_lo, b0) - b0);
-      if (b1 > b0) {
+      hdr->desc[bi] = make_int2(piece_p, desc);
+      if (bytes) {
         fence_proxy_async();
-        mbar_expect_tx(&hdr->bar[bi], (uint32_t)(b1 - b0));
-        bulk_g2s(bufs + (size_t)bi * p.buf_bytes, p.K + b0, (uint32_t)(b1 - b0), &hdr->bar[bi]);
+        mbar_expect_tx(&hdr->bar[bi], bytes);
+        bulk_g2s(bufs + (size_t)bi * p.buf_bytes, b0, bytes, &hdr->bar[bi]);
       }
     }
     cp += nb;
-    posp = pend;
-    if (cp == n && posp < endp) {
+    srcp = e1;
+    if (cp == n && remp > 0) {
       if (m > 2 && next_sorted(m - 2, n, Qp)) cp = Qp[m - 3];
+      else remp = 0;
     }
     ++j_issue;
     bi_issue = (bi_issue + 1 == NB) ? 0 : bi_issue + 1;
@@ -521,6 +546,8 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
   double S_v = 0.0, S_d = 0.0;
 
   // triangle state
+  int32_t Q[kMaxOrder];
+  int c = 0, piece_c = -1;
   int b = -1;   // last value of Q (-1: m = 2, no first row)
   int kb = 0;   // multiplicity of b in Q
   CT Mprime = CT(2), Mf = CT(2), inv_first = CT(0.5);
@@ -597,25 +624,21 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
     const int bi = bi_cons;
     const uint32_t parity = ph_cons;
     __syncwarp();
-    const int nb = hdr->nb[bi];
-    const int piece = hdr->piece[bi];
-    if (piece != piece_c) {
+    const int2 dsc = hdr->desc[bi];
+    const int nb = dsc.y & 31;
+    if (dsc.x != piece_c) {
       // this block starts a new piece: restart the compute cursor there
       if (open) flush_triangle();
-      const WarpPlan &pl = p.plan[piece];
+      const WarpPlan &pl = p.plan[dsc.x];
       for (int j = 0; j < kMaxOrder; ++j) Q[j] = pl.t[j];
       c = pl.t[m - 2];
-      pos = pl.start;
-      end = pl.end;
-      piece_c = piece;
+      piece_c = dsc.x;
       setup_triangle();
       open = true;
     }
     const int L0 = n - c;
-    const int64_t pend = pos + (int64_t)(nb * L0 - (nb * (nb - 1)) / 2);
-    const int flags = hdr->flags[bi];
     unsigned char *buf = bufs + (size_t)bi * p.buf_bytes;
-    if (flags & 1) {
+    if (dsc.y & kDescBulk) {
       const bool ok = mbar_wait_bounded(&hdr->bar[bi], parity);
       if (!__all_sync(0xffffffffu, ok)) {
         if (lane == 0) {
@@ -626,12 +649,10 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
         break;
       }
     }
-    if (flags >> 8) {
-      // bytes past the last 16-byte boundary of the array: plain loads
-      const int nt = flags >> 8, dst = hdr->tdst[bi];
-      if (lane < nt) buf[dst + lane] = p.K[tail_lo + lane];
+    if (dsc.y & kDescTail) {
+      const int nt = hdr->tlen[bi], dst = hdr->tcut[bi];
+      if (lane < nt) buf[dst + lane] = tail_ptr[lane];
     }
-    const int boff = hdr->boff[bi];
     ++j_cons;
     if (++bi_cons == NB) {
       bi_cons = 0;
@@ -642,107 +663,115 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
     issue_next();
 
     // ---------------------------------------------------- rows of the block
-    const ST *bp = reinterpret_cast<const ST *>(buf) + boff;
+    const ST *bp = reinterpret_cast<const ST *>(buf) + ((dsc.y >> 5) & 15);
+    // lane i (and i + 16) holds row i: its head, alpha and coefficients
+    const int ri = lane & 15;
+    const bool live = ri < nb;
+    const int ci = min(c + ri, n - 1);
+    const N ac = alpha_at(ci);
+    const bool first = ci == b;
+    const N coef = first ? cAf : cA;
+    const int rowend = live ? (L0 - 1) + ri * L0 - ((ri * (ri + 1)) >> 1) : L0 - 1;
+    const int rsl = live ? L0 - ri - 1 : 0;
+    const CT hv = ld_elem<ST, CT>(bp + (rowend - rsl));
     if (lane < kRB) {
-      // row data, one lane per row
-      const int i = lane;
-      const bool live = i < nb;
-      const int cr = min(c + i, n - 1);
-      const N cfi = live ? ((cr == b) ? cAf : cA) * alpha_at(cr) : mk<CT, D>(CT(0), CT(0));
-      RowInfo<CT> ri;
-      ri.cf_v = cfi.v;
-      ri.cf_d = cfi.d;
       // rows past the block's end read row 0's (finite) entries with a zero
       // coefficient, so the unmasked chunks stay harmless
-      ri.rowend = live ? (L0 - 1) + i * L0 - (i * (i + 1)) / 2 : L0 - 1;
-      ri.sl = live ? L0 - i - 1 : 0;
-      rinfo[i] = ri;
+      const N cfi = live ? coef * ac : mk<CT, D>(CT(0), CT(0));
+      RowInfo<CT> rw;
+      rw.cf_v = cfi.v;
+      rw.cf_d = cfi.d;
+      rw.rowend = rowend;
+      rw.sl = rsl;
+      rinfo[lane] = rw;
     }
     __syncwarp();
+    N dot[4];
     for (int r = 0; r < nb; r += 4) {
       // four rows at a time: their lengths differ by at most 3, so the chunk
       // count of the longest serves all four; only its top two chunks can run
       // past a row's end and need masks
-      N cf[4], dot[4];
+      N cf[4];
       int sl[4];
       const ST *prow[4];
+      CT xa[4], xb[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const RowInfo<CT> ri = rinfo[r + i];
-        cf[i] = mk<CT, D>(ri.cf_v, ri.cf_d);
-        sl[i] = ri.sl;
-        prow[i] = bp + (ri.rowend - lane);
+        const RowInfo<CT> rw = rinfo[r + i];
+        cf[i] = mk<CT, D>(rw.cf_v, rw.cf_d);
+        sl[i] = rw.sl;
+        prow[i] = bp + (rw.rowend - lane);
         dot[i] = mk<CT, D>(CT(0), CT(0));
       }
       // enter at the top chunk (two masked chunks), continue down the
       // unmasked chain to chunk 0
       switch ((sl[0] + 31) >> 5) {
-        case 1: quad_chunk<0, true>(acc, dot, ar, prow, sl, lane, cf); goto chunks_done;
-        case 2: quad_chunk<1, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<0, true>(acc, dot, ar, prow, sl, lane, cf); goto chunks_done;
-        case 3: quad_chunk<2, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<1, true>(acc, dot, ar, prow, sl, lane, cf); goto full_0;
-        case 4: quad_chunk<3, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<2, true>(acc, dot, ar, prow, sl, lane, cf); goto full_1;
-        case 5: quad_chunk<4, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<3, true>(acc, dot, ar, prow, sl, lane, cf); goto full_2;
-        case 6: quad_chunk<5, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<4, true>(acc, dot, ar, prow, sl, lane, cf); goto full_3;
-        case 7: quad_chunk<6, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<5, true>(acc, dot, ar, prow, sl, lane, cf); goto full_4;
-        case 8: quad_chunk<7, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<6, true>(acc, dot, ar, prow, sl, lane, cf); goto full_5;
-        case 9: quad_chunk<8, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<7, true>(acc, dot, ar, prow, sl, lane, cf); goto full_6;
-        case 10: quad_chunk<9, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<8, true>(acc, dot, ar, prow, sl, lane, cf); goto full_7;
-        case 11: quad_chunk<10, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<9, true>(acc, dot, ar, prow, sl, lane, cf); goto full_8;
-        case 12: quad_chunk<11, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<10, true>(acc, dot, ar, prow, sl, lane, cf); goto full_9;
-        case 13: quad_chunk<12, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<11, true>(acc, dot, ar, prow, sl, lane, cf); goto full_10;
-        case 14: quad_chunk<13, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<12, true>(acc, dot, ar, prow, sl, lane, cf); goto full_11;
-        case 15: quad_chunk<14, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<13, true>(acc, dot, ar, prow, sl, lane, cf); goto full_12;
-        case 16: quad_chunk<15, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<14, true>(acc, dot, ar, prow, sl, lane, cf); goto full_13;
-        case 17: quad_chunk<16, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<15, true>(acc, dot, ar, prow, sl, lane, cf); goto full_14;
-        case 18: quad_chunk<17, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<16, true>(acc, dot, ar, prow, sl, lane, cf); goto full_15;
-        case 19: quad_chunk<18, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<17, true>(acc, dot, ar, prow, sl, lane, cf); goto full_16;
-        case 20: quad_chunk<19, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<18, true>(acc, dot, ar, prow, sl, lane, cf); goto full_17;
-        case 21: quad_chunk<20, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<19, true>(acc, dot, ar, prow, sl, lane, cf); goto full_18;
-        case 22: quad_chunk<21, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<20, true>(acc, dot, ar, prow, sl, lane, cf); goto full_19;
-        case 23: quad_chunk<22, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<21, true>(acc, dot, ar, prow, sl, lane, cf); goto full_20;
-        case 24: quad_chunk<23, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<22, true>(acc, dot, ar, prow, sl, lane, cf); goto full_21;
-        case 25: quad_chunk<24, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<23, true>(acc, dot, ar, prow, sl, lane, cf); goto full_22;
-        case 26: quad_chunk<25, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<24, true>(acc, dot, ar, prow, sl, lane, cf); goto full_23;
-        case 27: quad_chunk<26, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<25, true>(acc, dot, ar, prow, sl, lane, cf); goto full_24;
-        case 28: quad_chunk<27, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<26, true>(acc, dot, ar, prow, sl, lane, cf); goto full_25;
-        case 29: quad_chunk<28, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<27, true>(acc, dot, ar, prow, sl, lane, cf); goto full_26;
-        case 30: quad_chunk<29, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<28, true>(acc, dot, ar, prow, sl, lane, cf); goto full_27;
-        case 31: quad_chunk<30, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<29, true>(acc, dot, ar, prow, sl, lane, cf); goto full_28;
-        case 32: quad_chunk<31, true>(acc, dot, ar, prow, sl, lane, cf); quad_chunk<30, true>(acc, dot, ar, prow, sl, lane, cf); goto full_29;
+        case 1: quad_load<0, NC>(prow, sl, lane, xa); quad_step<0, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto chunks_done;
+        case 2: quad_load<1, NC>(prow, sl, lane, xb); quad_step<1, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<0, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto chunks_done;
+        case 3: quad_load<2, NC>(prow, sl, lane, xa); quad_step<2, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<1, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_0;
+        case 4: quad_load<3, NC>(prow, sl, lane, xb); quad_step<3, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<2, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_1;
+        case 5: quad_load<4, NC>(prow, sl, lane, xa); quad_step<4, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<3, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_2;
+        case 6: quad_load<5, NC>(prow, sl, lane, xb); quad_step<5, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<4, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_3;
+        case 7: quad_load<6, NC>(prow, sl, lane, xa); quad_step<6, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<5, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_4;
+        case 8: quad_load<7, NC>(prow, sl, lane, xb); quad_step<7, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<6, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_5;
+        case 9: quad_load<8, NC>(prow, sl, lane, xa); quad_step<8, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<7, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_6;
+        case 10: quad_load<9, NC>(prow, sl, lane, xb); quad_step<9, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<8, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_7;
+        case 11: quad_load<10, NC>(prow, sl, lane, xa); quad_step<10, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<9, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_8;
+        case 12: quad_load<11, NC>(prow, sl, lane, xb); quad_step<11, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<10, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_9;
+        case 13: quad_load<12, NC>(prow, sl, lane, xa); quad_step<12, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<11, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_10;
+        case 14: quad_load<13, NC>(prow, sl, lane, xb); quad_step<13, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<12, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_11;
+        case 15: quad_load<14, NC>(prow, sl, lane, xa); quad_step<14, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<13, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_12;
+        case 16: quad_load<15, NC>(prow, sl, lane, xb); quad_step<15, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<14, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_13;
+        case 17: quad_load<16, NC>(prow, sl, lane, xa); quad_step<16, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<15, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_14;
+        case 18: quad_load<17, NC>(prow, sl, lane, xb); quad_step<17, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<16, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_15;
+        case 19: quad_load<18, NC>(prow, sl, lane, xa); quad_step<18, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<17, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_16;
+        case 20: quad_load<19, NC>(prow, sl, lane, xb); quad_step<19, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<18, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_17;
+        case 21: quad_load<20, NC>(prow, sl, lane, xa); quad_step<20, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<19, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_18;
+        case 22: quad_load<21, NC>(prow, sl, lane, xb); quad_step<21, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<20, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_19;
+        case 23: quad_load<22, NC>(prow, sl, lane, xa); quad_step<22, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<21, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_20;
+        case 24: quad_load<23, NC>(prow, sl, lane, xb); quad_step<23, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<22, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_21;
+        case 25: quad_load<24, NC>(prow, sl, lane, xa); quad_step<24, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<23, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_22;
+        case 26: quad_load<25, NC>(prow, sl, lane, xb); quad_step<25, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<24, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_23;
+        case 27: quad_load<26, NC>(prow, sl, lane, xa); quad_step<26, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<25, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_24;
+        case 28: quad_load<27, NC>(prow, sl, lane, xb); quad_step<27, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<26, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_25;
+        case 29: quad_load<28, NC>(prow, sl, lane, xa); quad_step<28, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<27, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_26;
+        case 30: quad_load<29, NC>(prow, sl, lane, xb); quad_step<29, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<28, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_27;
+        case 31: quad_load<30, NC>(prow, sl, lane, xa); quad_step<30, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<29, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_28;
+        case 32: quad_load<31, NC>(prow, sl, lane, xb); quad_step<31, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<30, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_29;
         default: goto chunks_done;
       }
-    full_29: quad_chunk<29, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_28: quad_chunk<28, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_27: quad_chunk<27, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_26: quad_chunk<26, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_25: quad_chunk<25, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_24: quad_chunk<24, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_23: quad_chunk<23, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_22: quad_chunk<22, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_21: quad_chunk<21, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_20: quad_chunk<20, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_19: quad_chunk<19, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_18: quad_chunk<18, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_17: quad_chunk<17, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_16: quad_chunk<16, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_15: quad_chunk<15, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_14: quad_chunk<14, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_13: quad_chunk<13, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_12: quad_chunk<12, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_11: quad_chunk<11, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_10: quad_chunk<10, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_9: quad_chunk<9, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_8: quad_chunk<8, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_7: quad_chunk<7, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_6: quad_chunk<6, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_5: quad_chunk<5, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_4: quad_chunk<4, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_3: quad_chunk<3, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_2: quad_chunk<2, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_1: quad_chunk<1, false>(acc, dot, ar, prow, sl, lane, cf);
-    full_0: quad_chunk<0, false>(acc, dot, ar, prow, sl, lane, cf);
-    chunks_done:
-      {
+    full_29: quad_step<29, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+    full_28: quad_step<28, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+    full_27: quad_step<27, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+    full_26: quad_step<26, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+    full_25: quad_step<25, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+    full_24: quad_step<24, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+    full_23: quad_step<23, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+    full_22: quad_step<22, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+    full_21: quad_step<21, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+    full_20: quad_step<20, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+    full_19: quad_step<19, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+    full_18: quad_step<18, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+    full_17: quad_step<17, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+    full_16: quad_step<16, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+    full_15: quad_step<15, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+    full_14: quad_step<14, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+    full_13: quad_step<13, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+    full_12: quad_step<12, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+    full_11: quad_step<11, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+    full_10: quad_step<10, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+    full_9: quad_step<9, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+    full_8: quad_step<8, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+    full_7: quad_step<7, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+    full_6: quad_step<6, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+    full_5: quad_step<5, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+    full_4: quad_step<4, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+    full_3: quad_step<3, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+    full_2: quad_step<2, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+    full_1: quad_step<1, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+    full_0: quad_step<0, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+    chunks_done:;
+      if (nb > 4) {
         const int a = dsm_index(lane, r);
         if (sizeof(CT) == 4) {
           *reinterpret_cast<float4 *>(&dsm_v[a]) = make_float4(dot[0].v, dot[1].v, dot[2].v, dot[3].v);
@@ -756,47 +785,54 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
         }
       }
     }
-    __syncwarp();
 
     // ---------------------------------------------------- row dots and epilogue
-    {
-      const int r = lane & 15, h = lane >> 4;
+    // the dot of row i ends on lane i
+    N s;
+    if (nb <= 4) {
+      // one quad: butterfly over the four dots (no shared memory)
+      const bool hi = (lane & 16) != 0, b8 = (lane & 8) != 0;
+      const N k0 = (hi ? dot[2] : dot[0]) + shfl_xor(hi ? dot[0] : dot[2], 16);
+      const N k1 = (hi ? dot[3] : dot[1]) + shfl_xor(hi ? dot[1] : dot[3], 16);
+      N k = (b8 ? k1 : k0) + shfl_xor(b8 ? k0 : k1, 8);
+      k = k + shfl_xor(k, 4);
+      k = k + shfl_xor(k, 2);
+      k = k + shfl_xor(k, 1);
+      // lane l holds row 2 (l >> 4 & 1) + (l >> 3 & 1)
+      s = shfl_idx(k, ((lane & 2) << 3) | ((lane & 1) << 3));
+    } else {
+      __syncwarp();
+      const int h = lane >> 4;
       // sixteen partials in registers, then a pairwise tree (short dependence chain)
       N t[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        const int a = dsm_index(16 * h + i, r);
+        const int a = dsm_index(16 * h + i, ri);
         t[i] = mk<CT, D>(dsm_v[a], D ? dsm_d[a] : CT(0));
       }
 #pragma unroll
       for (int w2 = 8; w2 >= 1; w2 >>= 1)
 #pragma unroll
         for (int i = 0; i < w2; ++i) t[i] = t[i] + t[i + w2];
-      N s = t[0];
-      s = s + shfl_xor(s, 16);
-      if (h == 0 && r < nb) {
-        const int ci = c + r;
-        const N ac = alpha_at(ci);
-        const int head = r * L0 - (r * (r - 1)) / 2;  // index of row r's head
-        const CT hv = ld_elem<ST, CT>(bp + head);
-        const bool first = (ci == b);
-        const CT cnt = first ? CT(kb + 1) : CT(1);
-        const N Rf = s + scale(hv * (first ? inv_first : CT(0.5)), ac);
-        const N gadd = (first ? cAf : cA) * (scale(hv, ac) + scale(cnt, s));
-        g_v[ci] += gadd.v;
-        if (D) g_d[ci] += gadd.d;
-        const N tadd = scale(first ? Mf : Mprime, ac * Rf);
-        if (first) Tfirst = Tfirst + tadd; else Trest = Trest + tadd;
-      }
+      s = t[0] + shfl_xor(t[0], 16);
+    }
+    if (lane < nb) {
+      const CT cnt = first ? CT(kb + 1) : CT(1);
+      const N Rf = s + scale(hv * (first ? inv_first : CT(0.5)), ac);
+      const N gadd = coef * (scale(hv, ac) + scale(cnt, s));
+      g_v[ci] += gadd.v;
+      if (D) g_d[ci] += gadd.d;
+      const N tadd = scale(first ? Mf : Mprime, ac * Rf);
+      if (first) Tfirst = Tfirst + tadd;
+      else Trest = Trest + tadd;
     }
 
     // ---------------------------------------------------- advance
     c += nb;
-    pos = pend;
     if (c == n) {
       flush_triangle();
       open = false;
-      if (pos < end) {
+      if (!(dsc.y & kDescLast)) {
         if (m > 2 && next_sorted(m - 2, n, Q)) {
           c = Q[m - 3];
           setup_triangle();
