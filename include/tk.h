@@ -154,7 +154,9 @@ int tk_contract_range(int m, int64_t n, int storage_dtype, const void *K_range,
 /* Launch configuration of the streaming contraction kernel.  Zero fields keep
  * the library's choice.
  *   warps        warps per block (each warp walks its own row-aligned piece)
- *   block_log2   log2 of the byte budget of one row block (one bulk copy)
+ *   block_bytes  bytes of one staging buffer (one bulk copy per row block), a
+ *                multiple of 128 in [1024, 65536]; 0 = the largest that fits
+ *                the shared memory with `warps` warps
  *   nbuf         staging buffers per warp (nbuf-1 copies in flight), 2..8
  *   ctas_per_sm  blocks per SM (1 or 2)
  *   row_cost     cost of one row, in entries, when the range is cut into pieces
@@ -167,7 +169,7 @@ int tk_contract_range(int m, int64_t n, int storage_dtype, const void *K_range,
  *                bits).  0 = library choice (1). */
 typedef struct {
     int warps;
-    int block_log2;
+    int block_bytes;
     int nbuf;
     int ctas_per_sm;
     int row_cost;

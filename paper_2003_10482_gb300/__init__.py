@@ -180,18 +180,18 @@ def workspace(m: int, n: int, B: int = 1, device=None) -> torch.Tensor:
 
 
 class tk_contract_config(ctypes.Structure):
-    _fields_ = [("warps", ctypes.c_int), ("block_log2", ctypes.c_int), ("nbuf", ctypes.c_int),
+    _fields_ = [("warps", ctypes.c_int), ("block_bytes", ctypes.c_int), ("nbuf", ctypes.c_int),
                 ("ctas_per_sm", ctypes.c_int), ("row_cost", ctypes.c_int), ("tri_cost", ctypes.c_int),
                 ("pieces_per_warp", ctypes.c_int), ("schedule", ctypes.c_int)]
 
 
-def tk_contract_set_config(warps=0, block_log2=0, nbuf=0, ctas_per_sm=0, row_cost=0, tri_cost=0,
+def tk_contract_set_config(warps=0, block_bytes=0, nbuf=0, ctas_per_sm=0, row_cost=0, tri_cost=0,
                            pieces_per_warp=0, schedule=0, reset=False):
     """Process-wide launch configuration of the contraction (0 = library choice)."""
     if reset:
         _check(lib().tk_contract_set_config(None))
         return
-    c = tk_contract_config(warps, block_log2, nbuf, ctas_per_sm, row_cost, tri_cost, pieces_per_warp, schedule)
+    c = tk_contract_config(warps, block_bytes, nbuf, ctas_per_sm, row_cost, tri_cost, pieces_per_warp, schedule)
     _check(lib().tk_contract_set_config(ctypes.byref(c)))
 
 

@@ -231,7 +231,7 @@ int tk_contract_set_config(const tk_contract_config *cfg) {
     g_contract_cfg = tk_contract_config{0, 0, 0, 0, 0, 0, 0, 0};
     return TK_OK;
   }
-  if (cfg->warps < 0 || cfg->warps > 16 || (cfg->block_log2 != 0 && (cfg->block_log2 < 9 || cfg->block_log2 > 15)) ||
+  if (cfg->warps < 0 || cfg->warps > 16 || (cfg->block_bytes != 0 && (cfg->block_bytes < 1024 || cfg->block_bytes > 65536 || cfg->block_bytes % 128)) ||
       (cfg->nbuf != 0 && (cfg->nbuf < 2 || cfg->nbuf > 8)) || cfg->ctas_per_sm < 0 || cfg->ctas_per_sm > 2 ||
       cfg->row_cost < 0 || cfg->tri_cost < 0 || cfg->pieces_per_warp < 0 || cfg->pieces_per_warp > 16 || cfg->schedule < 0 || cfg->schedule > 2)
     return fail(TK_EINVAL, "contract config out of range");

@@ -217,8 +217,7 @@ int plan_to_device(int m, int n, int64_t lo, int64_t hi, int pieces, int row_cos
 
 // ------------------------------------------------------------------ launch config
 struct Resolved {
-  int nc, warps, nbuf, buf_bytes, cap, vec_bytes, warp_bytes, grid, cps, row_cost, tri_cost, block_log2, ppw,
-      schedule;
+  int nc, warps, nbuf, buf_bytes, cap, vec_bytes, warp_bytes, grid, cps, row_cost, tri_cost, ppw, schedule;
   size_t smem;
 };
 
@@ -232,12 +231,6 @@ static int resolve(int m, int n, int storage, bool dual, Resolved *r) {
   r->nc = pick_nc(n);
   if (r->nc < 0) return fail(TK_EUNSUPPORTED, "contract: n=%d exceeds %d", n, TK_MAX_POINTS);
   const tk_contract_config &o = g_contract_cfg;
-  int bl = o.block_log2 > 0 ? o.block_log2 : 12;
-  if (bl < 9 || bl > 15) return fail(TK_EINVAL, "block_log2 outside [9, 15]");
-  while ((1 << bl) < n * es) ++bl;  // one full row must fit a block
-  r->block_log2 = bl;
-  r->cap = (1 << bl) / es;
-  r->buf_bytes = (((1 << bl) + 32) + 127) & ~127;
   r->nbuf = o.nbuf > 0 ? o.nbuf : 2;
   if (r->nbuf < 2 || r->nbuf > 8) return fail(TK_EINVAL, "nbuf outside [2, 8]");
   const int fixed = cts == 8 ? (dual ? warp_fixed_bytes<double, true>() : warp_fixed_bytes<double, false>())
@@ -245,18 +238,28 @@ static int resolve(int m, int n, int storage, bool dual, Resolved *r) {
   const int gbytes = ((dual ? 2 : 1) * n * cts + 127) & ~127;
   // staged vectors, then the rows-fit table (n+1 shorts) at the end of the region
   r->vec_bytes = ((dual ? 2 : 1) * n * cts + 2 * (n + 1) + 2 + 127) & ~127;
-  r->warp_bytes = fixed + gbytes + r->nbuf * r->buf_bytes;
-  r->warp_bytes = (r->warp_bytes + 127) & ~127;
   r->cps = o.ctas_per_sm > 0 ? o.ctas_per_sm : 1;
   if (r->cps > 2) return fail(TK_EINVAL, "ctas_per_sm must be 1 or 2");
   // keep 4 KB for the kernel's static shared memory (warp S partials, final reduction)
   const int smem_budget = (di.smem_optin - 4096) / r->cps;
-  const int warps_fit = (smem_budget - r->vec_bytes) / r->warp_bytes;
+  // a buffer holds one full row (n entries) plus the alignment slack of its copy
+  const int min_buf = (n * es + 32 + 127) & ~127;
   int warps = o.warps > 0 ? o.warps : kMaxWarps;
   warps = std::min(warps, max_threads_est(cts, dual, r->nc) / 32);
-  warps = std::min(warps, warps_fit);
+  int buf = 0;
+  for (; warps >= 1; --warps) {
+    const int per_warp = (smem_budget - r->vec_bytes) / warps;
+    const int room = ((per_warp - fixed - gbytes) / r->nbuf) & ~127;
+    buf = o.block_bytes > 0 ? o.block_bytes : std::min(room, 32768);
+    if (buf >= min_buf && buf <= room) break;
+    if (o.block_bytes > 0 && o.block_bytes < min_buf)
+      return fail(TK_EINVAL, "block_bytes %d below one row (%d bytes)", o.block_bytes, min_buf);
+  }
   if (warps < 1) return fail(TK_EUNSUPPORTED, "contract: shared memory too small for one warp");
   r->warps = warps;
+  r->buf_bytes = buf;
+  r->cap = (buf - 32) / es;
+  r->warp_bytes = (fixed + gbytes + r->nbuf * r->buf_bytes + 127) & ~127;
   r->grid = di.sms * r->cps;
   r->smem = (size_t)r->vec_bytes + (size_t)warps * r->warp_bytes;
   r->row_cost = o.row_cost > 0 ? o.row_cost : 256;
@@ -273,7 +276,7 @@ int contract_resolve(int m, int n, int storage, bool dual, tk_contract_config *o
   int rc = resolve(m, n, storage, dual, &r);
   if (rc != TK_OK) return rc;
   out->warps = r.warps;
-  out->block_log2 = r.block_log2;
+  out->block_bytes = r.buf_bytes;
   out->nbuf = r.nbuf;
   out->ctas_per_sm = r.cps;
   out->row_cost = r.row_cost;

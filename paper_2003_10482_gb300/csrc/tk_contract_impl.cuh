@@ -21,20 +21,24 @@
 // numbers) gives d/deps K[(a+eps v)^{m-1}] = (m-1) K[a^{m-2}, v] in the same
 // pass.
 //
-// GB300 mapping.  The host cuts the packed range into one row-aligned piece
-// per warp, balanced by cost (entries + a weight per row + a weight per
-// triangle, tk_contract_plan).  Each warp walks its rows in blocks of at most
-// 16 consecutive rows of one triangle whose entries fit a byte budget; every
-// block is fetched by one cp.async.bulk copy (TMA bulk engine, mbarrier
-// completion) into one of NBUF linear shared-memory buffers, so NBUF-1 blocks
-// are always in flight while the warp computes on the current one.  Within a
-// row, lane j owns the columns d = n-1-(32k+j): the last index is counted from
-// the end of the row, so every row of a triangle starts at chunk 0 and the
-// per-entry scatter to g_d accumulates in registers (acc[k]) with no atomics.
-// The per-lane partial row dots of a block go to a padded shared-memory tile
-// and are summed two lanes per row; the per-row epilogue runs on 16 lanes in
-// parallel.  Per-warp partial g lives in shared memory; blocks write FP64
-// partials that a second kernel sums in a fixed order.
+// GB300 mapping.  The host cuts the packed range into row-aligned pieces
+// (16 per warp), balanced by cost (entries + a weight per row + a weight per
+// triangle, tk_contract_plan); warp w takes pieces w, w+W, ... (or the next
+// free one from a shared ticket).  Each warp walks its rows in blocks of at
+// most 32 consecutive rows of one triangle whose entries fit its staging
+// buffer; every block is fetched by one cp.async.bulk copy (TMA bulk engine,
+// mbarrier completion) into one of NBUF linear shared-memory buffers, so
+// NBUF-1 blocks are always in flight while the warp computes on the current
+// one.  The buffers take all the shared memory the 16 warps leave free.
+// Within a row, lane j owns the columns d = n-1-(32k+j): the last index is
+// counted from the end of the row, so every row of a triangle starts at chunk
+// 0 and the per-entry scatter to g_d accumulates in registers (acc[k]) with no
+// atomics.  Rows go four at a time; the loads of each 32-column chunk are
+// issued one step ahead of its multiply-adds.  The four partial row dots of a
+// quad are summed by a butterfly of shuffles that leaves row i's dot on lane
+// i, where the per-row epilogue runs (all rows of a block in parallel).
+// Per-warp partial g lives in shared memory; blocks write FP64 partials that
+// the last block to finish sums in a fixed order.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -60,6 +64,9 @@ __device__ __forceinline__ void fence_proxy_async() {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes)
                : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   uint32_t ok;
@@ -187,13 +194,8 @@ __device__ __forceinline__ CT ld_vec(const void *p, int dt, int i) {
 }
 
 
-constexpr int kRB = 16;  // rows per block (upper bound)
-
-// Dot tile: lane l's partial dot of row r sits at dsm_index(l, r); a lane's
-// four dots of a quad are contiguous (one 128-bit store), and the 16-lane
-// reduction reads it without bank conflicts.
-__device__ __forceinline__ int dsm_index(int l, int r) { return l * 20 + r + 16 * (l >> 4); }
-constexpr int kDsmLen = 32 * 20 + 16;
+constexpr int kRB = 16;    // rows per block of the batched kernel (upper bound)
+constexpr int kRows = 32;  // rows per block of the single-vector kernel (upper bound)
 
 struct KParams {
   int m, n;
@@ -231,16 +233,12 @@ constexpr int max_threads() {
 }
 
 // Per-warp shared-memory header: NBUF mbarriers and the descriptor of each
-// issued block: {piece, nb | boff << 5 | BULK | TAIL | LAST}.
-constexpr int kDescBulk = 1 << 9;   // a bulk copy was issued for the block
-constexpr int kDescTail = 1 << 10;  // its last bytes (past the array's last 16-byte boundary) are copied by hand
-constexpr int kDescLast = 1 << 11;  // the last block of its piece
+// issued block: {piece, nb | boff << 6 | LAST}.
+constexpr int kDescLast = 1 << 10;  // the last block of its piece
 struct WarpHdr {
   uint64_t bar[8];
   int2 desc[8];
-  int tcut[8];    // buffer byte offset of the hand-copied tail
-  int tlen[8];    // tail bytes
-  int pad[16];
+  int pad[32];
 };
 static_assert(sizeof(WarpHdr) == 256, "warp header");
 
@@ -255,8 +253,8 @@ struct __align__(16) RowInfo {
 
 template <typename CT, bool D>
 __host__ __device__ constexpr int warp_fixed_bytes() {
-  // header, row info, dot tile(s); 128-byte aligned
-  return ((256 + kRB * (int)sizeof(RowInfo<CT>) + (D ? 2 : 1) * kDsmLen * (int)sizeof(CT)) + 127) & ~127;
+  // header and row info; 128-byte aligned
+  return ((256 + kRows * (int)sizeof(RowInfo<CT>)) + 127) & ~127;
 }
 
 // rows of the block that starts at row c (position pos) of its triangle:
@@ -406,8 +404,6 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
   unsigned char *wb = smem + p.vec_bytes + (size_t)wid * p.warp_bytes;
   WarpHdr *hdr = reinterpret_cast<WarpHdr *>(wb);
   RowInfo<CT> *rinfo = reinterpret_cast<RowInfo<CT> *>(wb + 256);
-  CT *dsm_v = reinterpret_cast<CT *>(wb + 256 + kRB * sizeof(RowInfo<CT>));
-  CT *dsm_d = dsm_v + kDsmLen;
   CT *g_v = reinterpret_cast<CT *>(wb + warp_fixed_bytes<CT, D>());
   CT *g_d = g_v + n;
   const int gbytes = (int)((((D ? 2 : 1) * n * (int)sizeof(CT)) + 127) & ~127);
@@ -415,14 +411,14 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
   const int NB = p.nbuf;
 
   // rows of a block that starts with a row of length L (rows shrink by one):
-  // at most kRB, at most L, within `cap` entries
+  // at most kRows, at most L, within `cap` entries
   short *rfit = reinterpret_cast<short *>(smem + p.vec_bytes - 2 * (n + 1) - 2);
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     a_s[i] = ld_vec<CT>(p.alpha, p.vec_dtype, i);
     if (D) v_s[i] = ld_vec<CT>(p.v, p.vec_dtype, i);
   }
   for (int L = threadIdx.x; L <= n; L += blockDim.x) {
-    int r = min(kRB, L);
+    int r = min(kRows, L);
     while (r > 1 && r * L - (r * (r - 1)) / 2 > p.cap) --r;
     rfit[L] = (short)max(r, 1);
   }
@@ -500,28 +496,25 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
     const unsigned char *b0 = srcp - lead;
     const unsigned char *e1 = srcp + span * ES;
     uint32_t bytes = (lead + (uint32_t)(span * ES) + 15u) & ~15u;
-    int desc = nb | (int)((lead / ES) << 5);
     const int bi = bi_issue;
+    unsigned char *dst = bufs + (size_t)bi * p.buf_bytes;
     if (e1 > tail_ptr) {
-      // the block reaches past the array's last 16-byte boundary: the bytes
-      // from there are copied by hand (rare: the last block of the range)
-      const unsigned char *t0 = b0 > tail_ptr ? b0 : tail_ptr;
-      bytes = (uint32_t)(t0 - b0);
-      desc |= kDescTail;
-      if (lane == 0) {
-        hdr->tcut[bi] = (int)bytes;
-        hdr->tlen[bi] = (int)(e1 - t0);
-      }
+      // the block reaches past the array's last 16-byte boundary (the last
+      // block of the range): the bytes from there are copied by hand
+      bytes = (uint32_t)(tail_ptr - b0);
+      const int nt = (int)(e1 - tail_ptr);
+      if (lane < nt) dst[bytes + lane] = tail_ptr[lane];
+      __syncwarp();
     }
-    if (bytes) desc |= kDescBulk;
     remp -= span;
-    if (remp <= 0) desc |= kDescLast;
     if (lane == 0) {
-      hdr->desc[bi] = make_int2(piece_p, desc);
+      hdr->desc[bi] = make_int2(piece_p, nb | (int)((lead / ES) << 6) | (remp <= 0 ? kDescLast : 0));
       if (bytes) {
         fence_proxy_async();
         mbar_expect_tx(&hdr->bar[bi], bytes);
-        bulk_g2s(bufs + (size_t)bi * p.buf_bytes, b0, bytes, &hdr->bar[bi]);
+        bulk_g2s(dst, b0, bytes, &hdr->bar[bi]);
+      } else {
+        mbar_arrive(&hdr->bar[bi]);  // nothing to copy: complete the phase
       }
     }
     cp += nb;
@@ -625,7 +618,7 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
     const uint32_t parity = ph_cons;
     __syncwarp();
     const int2 dsc = hdr->desc[bi];
-    const int nb = dsc.y & 31;
+    const int nb = dsc.y & 63;
     if (dsc.x != piece_c) {
       // this block starts a new piece: restart the compute cursor there
       if (open) flush_triangle();
@@ -637,44 +630,35 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
       open = true;
     }
     const int L0 = n - c;
-    unsigned char *buf = bufs + (size_t)bi * p.buf_bytes;
-    if (dsc.y & kDescBulk) {
-      const bool ok = mbar_wait_bounded(&hdr->bar[bi], parity);
-      if (!__all_sync(0xffffffffu, ok)) {
-        if (lane == 0) {
-          atomicExch(&reinterpret_cast<WsHeader *>(p.status)->status, TK_ETIMEOUT);
-          reinterpret_cast<WsHeader *>(p.status)->where = 1;
-        }
-        failed = true;
-        break;
+    const unsigned char *buf = bufs + (size_t)bi * p.buf_bytes;
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&hdr->bar[bi], parity))) {
+      if (lane == 0) {
+        atomicExch(&reinterpret_cast<WsHeader *>(p.status)->status, TK_ETIMEOUT);
+        reinterpret_cast<WsHeader *>(p.status)->where = 1;
       }
-    }
-    if (dsc.y & kDescTail) {
-      const int nt = hdr->tlen[bi], dst = hdr->tcut[bi];
-      if (lane < nt) buf[dst + lane] = tail_ptr[lane];
+      failed = true;
+      break;
     }
     ++j_cons;
     if (++bi_cons == NB) {
       bi_cons = 0;
       ph_cons ^= 1u;
     }
-    __syncwarp();
     // the previous block's buffer is free again: keep NBUF-1 copies in flight
     issue_next();
 
     // ---------------------------------------------------- rows of the block
-    const ST *bp = reinterpret_cast<const ST *>(buf) + ((dsc.y >> 5) & 15);
-    // lane i (and i + 16) holds row i: its head, alpha and coefficients
-    const int ri = lane & 15;
-    const bool live = ri < nb;
-    const int ci = min(c + ri, n - 1);
+    const ST *bp = reinterpret_cast<const ST *>(buf) + ((dsc.y >> 6) & 15);
+    // lane i holds row i: its head, alpha and coefficients
+    const bool live = lane < nb;
+    const int ci = min(c + lane, n - 1);
     const N ac = alpha_at(ci);
     const bool first = ci == b;
     const N coef = first ? cAf : cA;
-    const int rowend = live ? (L0 - 1) + ri * L0 - ((ri * (ri + 1)) >> 1) : L0 - 1;
-    const int rsl = live ? L0 - ri - 1 : 0;
+    const int rowend = live ? (L0 - 1) + lane * L0 - ((lane * (lane + 1)) >> 1) : L0 - 1;
+    const int rsl = live ? L0 - lane - 1 : 0;
     const CT hv = ld_elem<ST, CT>(bp + (rowend - rsl));
-    if (lane < kRB) {
+    {
       // rows past the block's end read row 0's (finite) entries with a zero
       // coefficient, so the unmasked chunks stay harmless
       const N cfi = live ? coef * ac : mk<CT, D>(CT(0), CT(0));
@@ -686,12 +670,12 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
       rinfo[lane] = rw;
     }
     __syncwarp();
-    N dot[4];
+    N s = mk<CT, D>(CT(0), CT(0));  // the dot of row `lane`
     for (int r = 0; r < nb; r += 4) {
       // four rows at a time: their lengths differ by at most 3, so the chunk
       // count of the longest serves all four; only its top two chunks can run
       // past a row's end and need masks
-      N cf[4];
+      N cf[4], dot[4];
       int sl[4];
       const ST *prow[4];
       CT xa[4], xb[4];
@@ -771,52 +755,23 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
     full_1: quad_step<1, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
     full_0: quad_step<0, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
     chunks_done:;
-      if (nb > 4) {
-        const int a = dsm_index(lane, r);
-        if (sizeof(CT) == 4) {
-          *reinterpret_cast<float4 *>(&dsm_v[a]) = make_float4(dot[0].v, dot[1].v, dot[2].v, dot[3].v);
-          if (D) *reinterpret_cast<float4 *>(&dsm_d[a]) = make_float4(dot[0].d, dot[1].d, dot[2].d, dot[3].d);
-        } else {
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            dsm_v[a + i] = dot[i].v;
-            if (D) dsm_d[a + i] = dot[i].d;
-          }
-        }
+      {
+        // butterfly over the lanes: after it lane l holds the dot of row
+        // r + 2 (l >> 4 & 1) + (l >> 3 & 1); row r + i then moves to lane r + i
+        const bool hi = (lane & 16) != 0, b8 = (lane & 8) != 0;
+        const N k0 = (hi ? dot[2] : dot[0]) + shfl_xor(hi ? dot[0] : dot[2], 16);
+        const N k1 = (hi ? dot[3] : dot[1]) + shfl_xor(hi ? dot[1] : dot[3], 16);
+        N k = (b8 ? k1 : k0) + shfl_xor(b8 ? k0 : k1, 8);
+        k = k + shfl_xor(k, 4);
+        k = k + shfl_xor(k, 2);
+        k = k + shfl_xor(k, 1);
+        k = shfl_idx(k, ((lane & 2) << 3) | ((lane & 1) << 3));
+        if ((lane & ~3) == r) s = k;
       }
     }
 
-    // ---------------------------------------------------- row dots and epilogue
-    // the dot of row i ends on lane i
-    N s;
-    if (nb <= 4) {
-      // one quad: butterfly over the four dots (no shared memory)
-      const bool hi = (lane & 16) != 0, b8 = (lane & 8) != 0;
-      const N k0 = (hi ? dot[2] : dot[0]) + shfl_xor(hi ? dot[0] : dot[2], 16);
-      const N k1 = (hi ? dot[3] : dot[1]) + shfl_xor(hi ? dot[1] : dot[3], 16);
-      N k = (b8 ? k1 : k0) + shfl_xor(b8 ? k0 : k1, 8);
-      k = k + shfl_xor(k, 4);
-      k = k + shfl_xor(k, 2);
-      k = k + shfl_xor(k, 1);
-      // lane l holds row 2 (l >> 4 & 1) + (l >> 3 & 1)
-      s = shfl_idx(k, ((lane & 2) << 3) | ((lane & 1) << 3));
-    } else {
-      __syncwarp();
-      const int h = lane >> 4;
-      // sixteen partials in registers, then a pairwise tree (short dependence chain)
-      N t[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int a = dsm_index(16 * h + i, ri);
-        t[i] = mk<CT, D>(dsm_v[a], D ? dsm_d[a] : CT(0));
-      }
-#pragma unroll
-      for (int w2 = 8; w2 >= 1; w2 >>= 1)
-#pragma unroll
-        for (int i = 0; i < w2; ++i) t[i] = t[i] + t[i + w2];
-      s = t[0] + shfl_xor(t[0], 16);
-    }
-    if (lane < nb) {
+    // ---------------------------------------------------- row epilogue
+    if (live) {
       const CT cnt = first ? CT(kb + 1) : CT(1);
       const N Rf = s + scale(hv * (first ? inv_first : CT(0.5)), ac);
       const N gadd = coef * (scale(hv, ac) + scale(cnt, s));
