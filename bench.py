@@ -198,6 +198,72 @@ def run_reference(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def batched_leg(dev) -> dict:
+    """Dual solves/s of the batched FP32 path against plain FP64 solves.
+
+    Workload: m = 4, n' = 300 Nystrom landmarks (uniform without replacement,
+    tk_nystrom_select) of 20,000 points, d = 80; the lambda path is
+    logspace(-4, 0, 64) x 8 cross-validation folds (masks).  Timed here: the
+    16 largest lambdas (0.1 <= lambda <= 1) x 8 folds = 128 problems, where
+    the FP32 tensor resolves the objective to the 1e-7 target (for smaller
+    lambda the dual variables grow like |y_perp| / lambda and K[a^4] cancels
+    beyond FP32, and beyond FP64 near lambda = 1e-4).  Both arms run Newton-CG
+    to the same relative-gap target (1e-7) with the same 40-iteration cap:
+    batched = one tk_solve_dual call over the 128 problems on the FP32 tensor
+    (one pass serves the whole batch); plain = one FP64-tensor solve per
+    problem, timed on 8 of them.  Accuracy: F of each batched solution under
+    the FP64 tensor against the plain FP64 solve's F."""
+    import torch
+
+    import paper_2003_10482_gb300 as tk
+    import synth
+    p = synth.batched_path()
+    m = p["m"]
+    idx = tk.tk_nystrom_select(p["X"].shape[0], p["n_prime"], p["select_seed"])
+    X = torch.tensor(p["X"][idx], device=dev)
+    y = torch.tensor(p["y"][idx], device=dev)
+    n = X.shape[0]
+    sel = torch.arange(384, 512, device=dev)  # lambda indices 48..63, all folds
+    lam = torch.tensor(p["lambdas"], device=dev)[sel].contiguous()
+    mask = torch.tensor(p["masks"], device=dev)[sel].contiguous()
+    K32 = tk.tk_build_packed(X, m, storage="f32")
+    K64 = tk.tk_build_packed(X, m, storage="f64")
+    gap, iters = 1e-7, 40
+    tk.tk_solve_dual(K32, m, n, y, lam[:32], mask=mask[:32], tol=0.0, rel_gap=gap, max_iter=2)  # warm-up
+    tk.tk_solve_dual(K64, m, n, y, lam[:1], mask=mask[:1], tol=0.0, rel_gap=gap, max_iter=2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    A32, rep, _ = tk.tk_solve_dual(K32, m, n, y, lam, mask=mask, tol=0.0, rel_gap=gap, max_iter=iters)
+    torch.cuda.synchronize()
+    t_batched = time.perf_counter() - t0
+    B = lam.numel()
+    sample = list(range(0, B, B // 8))[:8]  # fold 0 of every second lambda
+    t_plain, errs, per_lambda = [], [], []
+    for j in sample:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        A64, r64, _ = tk.tk_solve_dual(K64, m, n, y, lam[j:j + 1], mask=mask[j:j + 1], tol=0.0, rel_gap=gap,
+                                       max_iter=iters)
+        torch.cuda.synchronize()
+        t_plain.append(time.perf_counter() - t0)
+        F, _, _ = tk.tk_objective(K64, m, n, A32[j].contiguous(), y, lam[j:j + 1])
+        e = abs(float(F[0]) - r64[0]["F"]) / abs(r64[0]["F"])
+        errs.append(e)
+        per_lambda.append({"lambda": float(lam[j]), "rel_obj_diff": e, "fp64_passes": r64[0]["passes"],
+                           "batched_passes": rep[j]["passes"]})
+    held_out = float(A32[~mask.bool()].abs().max()) if bool((~mask.bool()).any()) else 0.0
+    plain_s = statistics.mean(t_plain)
+    return {"workload": "batched_path_m4_np300_d80 (lambda in [0.1, 1] x 8 folds)", "problems": B,
+            "batched_fp32": {"solves_per_s": B / t_batched, "seconds": t_batched,
+                             "converged": sum(r["status"] == 0 for r in rep),
+                             "max_passes": max(r["passes"] for r in rep)},
+            "plain_fp64": {"solves_per_s": 1.0 / plain_s, "seconds_per_solve": plain_s, "timed_problems": len(sample)},
+            "speedup": (B / t_batched) * plain_s,
+            "target": "relative objective gap 1e-7 (Newton decrement), at most 40 Newton iterations",
+            "max_rel_obj_diff_vs_fp64": max(errs), "held_out_max_abs_alpha": held_out,
+            "per_lambda": per_lambda}
+
+
 def run_ours(args) -> None:
     import torch
     import torch.distributed as dist
@@ -331,6 +397,8 @@ def run_ours(args) -> None:
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_leg()
+        if world == 1 and not args.no_batched:
+            line["batched"] = batched_leg(dev)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -344,6 +412,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-vs-FP64 dual-solve comparison")
     ap.add_argument("--n", type=int, default=0,
                     help="points of the workload (default: all 400); smaller n for profiler captures")
     args = ap.parse_args()

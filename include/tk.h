@@ -134,8 +134,10 @@ size_t tk_contract_workspace_size(int m, int64_t n, int64_t B);
  * A, V, G: B x n row-major, vec_dtype TK_F64 or TK_F32.  S: B FP64 values.
  * Arithmetic: FP64 for TK_F64 storage; FP32 for TK_F32 / TK_BF16 storage with
  * the cross-block reduction and S in FP64.  Each packed entry is read from
- * HBM once per pass; B > 1 loops over the batch (see tk_contract_batched for
- * one pass over all B).  Asynchronous; errors that only the device can see
+ * HBM once per pass.  For TK_F32 / TK_BF16 storage and B >= 28 (B >= 16 for
+ * r = m-2) one launch serves the whole batch (each entry read once for all B
+ * vectors, 2B multiply-adds per entry; 4B for r = m-2); otherwise the
+ * single-vector pass runs once per b.  Asynchronous; errors that only the device can see
  * (a bounded wait that ran out) are recorded in `work` and returned by
  * tk_status_read. */
 int tk_contract(int m, int64_t n, int storage_dtype, const void *K, int64_t B,
@@ -290,6 +292,10 @@ typedef struct {
     int max_iter;           /* outer iterations */
     int max_cg;             /* conjugate-gradient steps per Newton step */
     double armijo_c;        /* sufficient-decrease constant (0: 1e-4) */
+    double tol_rel_gap;     /* Newton-CG: also stop a problem when its Newton decrement
+                               estimate -<grad F, p>/2 (p the inner-solve direction,
+                               F(a) - F* to second order) is <= tol_rel_gap * max(1, |F|);
+                               0 = off */
 } tk_solve_opts;
 
 typedef struct {
@@ -307,12 +313,20 @@ size_t tk_solve_workspace_size(const tk_problem *P);
  * device; masked entries are zeroed), in FP64 vector arithmetic on the device:
  *   Newton-CG:  H p = -grad F by conjugate gradients with forcing term
  *               min(0.5, sqrt|grad F|), H v = (m-1) K[a^{m-2}, v] + lambda v,
- *               then Armijo backtracking on F (halving the step);
+ *               then backtracking (halving the step) until either Armijo's
+ *               sufficient decrease holds or <grad F(a + t p), p> <= 0 (F is
+ *               convex along the line, so the latter certifies F(a + t p) <=
+ *               F(a) from gradients alone when F's rounding noise hides the
+ *               decrease);
  *   GD_BT:      steepest descent with Armijo backtracking, step initialised
  *               from the previous accepted step.
  * Every objective is one contraction pass and every H v one dual-number pass
  * (tk_contract with r = m-2).  Writes one report per problem (host array of
- * B entries); returns TK_ENOTCONV if any problem missed tol.  Synchronises
+ * B entries); returns TK_ENOTCONV if any problem missed tol (a problem also
+ * stops, unconverged, after 8 iterations in which neither F fell by more
+ * than its rounding level under Armijo's test nor |grad F| fell below 0.999
+ * of its best value: the rounding floor of the contraction, which rises with
+ * |a|^{m-1}, has been reached).  Synchronises
  * `stream` once per step to read the per-problem scalars. */
 int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double *A_inout, tk_solve_report *R_host,
                   void *work, size_t work_bytes, void *stream);

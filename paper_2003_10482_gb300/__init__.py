@@ -327,7 +327,7 @@ class tk_problem(ctypes.Structure):
 
 class tk_solve_opts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("tol_gradnorm", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("max_cg", ctypes.c_int), ("armijo_c", ctypes.c_double)]
+                ("max_cg", ctypes.c_int), ("armijo_c", ctypes.c_double), ("tol_rel_gap", ctypes.c_double)]
 
 
 class tk_solve_report(ctypes.Structure):
@@ -340,9 +340,11 @@ _solve_ws: dict = {}
 
 def tk_solve_dual(K: torch.Tensor, m: int, n: int, y: torch.Tensor, lam, alpha0: torch.Tensor | None = None,
                   mask: torch.Tensor | None = None, method: str = "newton_cg", tol: float = 1e-10,
-                  max_iter: int = 100, max_cg: int = 0, stream=None):
+                  max_iter: int = 100, max_cg: int = 0, rel_gap: float = 0.0, stream=None):
     """Solve B dual problems over the packed tensor K.  Returns (alpha (B x n FP64),
-    reports (list of dicts), rc) where rc is TK_OK or TK_ENOTCONV."""
+    reports (list of dicts), rc) where rc is TK_OK or TK_ENOTCONV.  A problem
+    stops when |grad F| <= tol or (Newton-CG, rel_gap > 0) when its Newton
+    decrement estimate of F - F* is <= rel_gap * max(1, |F|)."""
     dev = K.device
     lam_t = torch.as_tensor(lam, dtype=torch.float64, device=dev).reshape(-1).contiguous()
     B = lam_t.numel()
@@ -352,7 +354,7 @@ def tk_solve_dual(K: torch.Tensor, m: int, n: int, y: torch.Tensor, lam, alpha0:
     mk = None if mask is None else mask.reshape(B, n).to(dev, torch.uint8).contiguous()
     prob = tk_problem(m, n, dtype_code(K.dtype), K.data_ptr(), yd.data_ptr(), B, lam_t.data_ptr(),
                       0 if mk is None else mk.data_ptr())
-    opts = tk_solve_opts(TK_NEWTON_CG if method == "newton_cg" else TK_GD_BT, tol, max_iter, max_cg, 0.0)
+    opts = tk_solve_opts(TK_NEWTON_CG if method == "newton_cg" else TK_GD_BT, tol, max_iter, max_cg, 0.0, rel_gap)
     need = int(lib().tk_solve_workspace_size(ctypes.byref(prob)))
     if need == 0:
         raise TKError(TK_EINVAL, lib().tk_last_error().decode())

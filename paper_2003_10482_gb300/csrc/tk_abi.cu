@@ -160,14 +160,17 @@ static int contract_impl(int m, int64_t n, int storage, const void *K, int64_t o
   if (rc != TK_OK) return rc;
   const size_t need = contract_workspace_bytes((int)n, di.sms);
   if (work_bytes < need) return fail(TK_ENOMEM, "workspace %zu < %zu bytes", work_bytes, need);
-  const bool use_batched_ws = B > 1 && work_bytes >= batched_workspace_bytes((int)n, B, di.sms);
-  (void)use_batched_ws;
 
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int vs = vec_dtype == TK_F64 ? 8 : 4;
   unsigned char *wsb = reinterpret_cast<unsigned char *>(work);
-  if (B > 1 && storage != TK_F64) {
-    // one pass for the whole batch when the batched kernel covers the shape
+  // One pass for the whole batch when the batched kernel covers the shape and
+  // the batch is large enough to pay for it: its launch costs about as much
+  // for one vector as for 64 (32 for the HVP), while the single-vector kernel
+  // runs at the HBM rate (measured on GB300, m = 4, n = 300: the batched
+  // kernel wins from B = 28 for K[a^{m-1}] and from B = 16 for the HVP).
+  const int64_t min_batched = (r == m - 2) ? 16 : 28;
+  if (B >= min_batched && storage != TK_F64) {
     BatchedArgs ba;
     ba.m = m;
     ba.n = (int)n;

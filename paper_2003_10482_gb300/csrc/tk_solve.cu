@@ -96,12 +96,62 @@ __global__ void k_hvp_finish(int m, int64_t B, int n, const double *G, const dou
   Hd[i] = keep ? (m - 1) * G[i] + lambda[i / n] * d[i] : 0.0;
 }
 
+// dst_j = src_{idx_j}  (gathers the rows of the problems in a pass)
+__global__ void k_gather(int64_t nb, int n, const int *idx, const double *src, double *dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb * n) return;
+  const int64_t j = i / n;
+  dst[i] = src[(int64_t)idx[j] * n + (i - j * n)];
+}
+
+// k_assemble for the compacted problems: row j of G and S belongs to problem idx_j
+__global__ void __launch_bounds__(256) k_assemble_idx(int m, int n, const int *idx, const double *G,
+                                                      const double *S, const double *A, const double *y,
+                                                      const double *lambda, const uint8_t *mask, double *F,
+                                                      double *grad, double *gn2) {
+  __shared__ double sh[8];
+  const int64_t j = blockIdx.x;
+  const int64_t b = idx[j];
+  const double lam = lambda[b];
+  double ssq = 0.0, aa = 0.0, ya = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int64_t k = b * n + i;
+    const double a = A[k];
+    const bool keep = !mask || mask[k];
+    const double gr = keep ? G[j * n + i] + lam * a - y[i] : 0.0;
+    grad[k] = gr;
+    ssq += gr * gr;
+    aa += a * a;
+    ya += y[i] * a;
+  }
+  const double t0 = block_sum_fixed<256>(ssq, sh);
+  const double t1 = block_sum_fixed<256>(aa, sh);
+  const double t2 = block_sum_fixed<256>(ya, sh);
+  if (threadIdx.x == 0) {
+    F[b] = S[j] / m + 0.5 * lam * t1 - t2;
+    gn2[b] = t0;
+  }
+}
+
+// k_hvp_finish for the compacted problems
+__global__ void k_hvp_finish_idx(int m, int64_t nb, int n, const int *idx, const double *G, const double *d,
+                                 const double *lambda, const uint8_t *mask, double *Hd) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nb * n) return;
+  const int64_t j = i / n;
+  const int64_t b = idx[j];
+  const int64_t k = b * n + (i - j * n);
+  const bool keep = !mask || mask[k];
+  Hd[k] = keep ? (m - 1) * G[i] + lambda[b] * d[k] : 0.0;
+}
+
 // ------------------------------------------------------------------ host
 struct SolveWs {
   unsigned char *cws;  // contraction workspace
   size_t cws_bytes;
-  double *G, *g, *p, *r, *d, *Hd, *at, *gt;  // B x n each
+  double *G, *g, *p, *r, *d, *Hd, *at, *gt, *Ac, *dc;  // B x n each (Ac, dc: compacted rows)
   double *S, *F, *Ft, *gn2, *gn2t, *sc, *ca, *cb;  // B each
+  int *idx;                                         // B problem indices of a compacted pass
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -113,7 +163,7 @@ static size_t solve_layout(int64_t B, int64_t n, size_t cws_bytes, SolveWs *w, u
   if (w) {
     w->cws = base;
     w->cws_bytes = cws_bytes;
-    double **vs[] = {&w->G, &w->g, &w->p, &w->r, &w->d, &w->Hd, &w->at, &w->gt};
+    double **vs[] = {&w->G, &w->g, &w->p, &w->r, &w->d, &w->Hd, &w->at, &w->gt, &w->Ac, &w->dc};
     for (double **v : vs) {
       *v = reinterpret_cast<double *>(base + off);
       off += vec;
@@ -123,9 +173,11 @@ static size_t solve_layout(int64_t B, int64_t n, size_t cws_bytes, SolveWs *w, u
       *v = reinterpret_cast<double *>(base + off);
       off += sca;
     }
+    w->idx = reinterpret_cast<int *>(base + off);
+    off += align256((size_t)B * sizeof(int));
     return off;
   }
-  return off + 8 * vec + 8 * sca;
+  return off + 10 * vec + 8 * sca + align256((size_t)B * sizeof(int));
 }
 
 static inline unsigned grid_for(int64_t cnt) { return (unsigned)((cnt + 255) / 256); }
@@ -138,6 +190,42 @@ struct Solver {
   int n, m;
   std::vector<double> h_a, h_b;  // coefficient staging
 
+  // Objective (or HVP) of the problems in `list` only: their rows are gathered,
+  // contracted as one smaller batch and the results scattered back; rows of
+  // the other problems in F / grad / gn2 (or Hd) are left as they are.
+  int set_list(const std::vector<int> &list) {
+    TK_CUDA_CHECK(cudaMemcpyAsync(w.idx, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    return TK_OK;
+  }
+  int objective_sub(const std::vector<int> &list, const double *A, double *F, double *grad, double *gn2) {
+    const int64_t nb = (int64_t)list.size();
+    if (nb == 0) return TK_OK;
+    if (nb == B) return objective(A, F, grad, gn2);
+    int rc = set_list(list);
+    if (rc != TK_OK) return rc;
+    k_gather<<<grid_for(nb * n), 256, 0, st>>>(nb, n, w.idx, A, w.Ac);
+    TK_CUDA_CHECK(cudaGetLastError());
+    rc = tk_contract(m, n, P->storage_dtype, P->K, nb, TK_F64, w.Ac, m - 1, nullptr, w.G, w.S, w.cws, w.cws_bytes, st);
+    if (rc != TK_OK) return rc;
+    k_assemble_idx<<<(unsigned)nb, 256, 0, st>>>(m, n, w.idx, w.G, w.S, A, P->y, P->lambda, P->mask, F, grad, gn2);
+    TK_CUDA_CHECK(cudaGetLastError());
+    return TK_OK;
+  }
+  int hvp_sub(const std::vector<int> &list, const double *A, const double *d, double *Hd) {
+    const int64_t nb = (int64_t)list.size();
+    if (nb == 0) return TK_OK;
+    if (nb == B) return hvp(A, d, Hd);
+    int rc = set_list(list);
+    if (rc != TK_OK) return rc;
+    k_gather<<<grid_for(nb * n), 256, 0, st>>>(nb, n, w.idx, A, w.Ac);
+    k_gather<<<grid_for(nb * n), 256, 0, st>>>(nb, n, w.idx, d, w.dc);
+    TK_CUDA_CHECK(cudaGetLastError());
+    rc = tk_contract(m, n, P->storage_dtype, P->K, nb, TK_F64, w.Ac, m - 2, w.dc, w.G, nullptr, w.cws, w.cws_bytes, st);
+    if (rc != TK_OK) return rc;
+    k_hvp_finish_idx<<<grid_for(nb * n), 256, 0, st>>>(m, nb, n, w.idx, w.G, d, P->lambda, P->mask, Hd);
+    TK_CUDA_CHECK(cudaGetLastError());
+    return TK_OK;
+  }
   int objective(const double *A, double *F, double *grad, double *gn2) {
     int rc = tk_contract(m, n, P->storage_dtype, P->K, B, TK_F64, A, m - 1, nullptr, w.G, w.S, w.cws, w.cws_bytes, st);
     if (rc != TK_OK) return rc;
@@ -202,7 +290,7 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
   if (!P || !O || !A || !R || !work) return fail(TK_EINVAL, "NULL argument");
   if (P->B < 1 || !P->K || !P->y || !P->lambda) return fail(TK_EINVAL, "bad problem");
   if (O->method != TK_NEWTON_CG && O->method != TK_GD_BT) return fail(TK_EINVAL, "unknown method %d", O->method);
-  if (O->max_iter < 0 || O->tol_gradnorm < 0) return fail(TK_EINVAL, "bad options");
+  if (O->max_iter < 0 || O->tol_gradnorm < 0 || O->tol_rel_gap < 0) return fail(TK_EINVAL, "bad options");
   const size_t need = tk_solve_workspace_size(P);
   if (need == 0) return TK_EINVAL;
   if (work_bytes < need) return fail(TK_ENOMEM, "workspace %zu < %zu bytes", work_bytes, need);
@@ -219,7 +307,11 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
   const int max_cg = O->max_cg > 0 ? O->max_cg : std::max(1, std::min(n, 200));
   const double tol = O->tol_gradnorm;
 
-  std::vector<double> F(B), gn2(B), Ft(B), gn2t(B), rr(B), rr_new(B), dHd(B), slope(B), t(B), gstep(B, 0.0);
+  std::vector<double> F(B), gn2(B), Ft(B), gn2t(B), rr(B), rr_new(B), dHd(B), slope(B), slope_t(B), t(B), gstep(B, 0.0);
+  // stall detection: best gradient norm so far and iterations since it last fell by 0.1 %
+  std::vector<double> best_gn2(B, 0.0);
+  std::vector<int> since_best(B, 0);
+  const int kStallIters = 8;
   std::vector<double> one(B, 1.0), zero(B, 0.0), minus1(B, -1.0), ca(B), cb(B), flag(B);
   std::vector<int> status(B, TK_ENOTCONV), iters(B, 0), passes(B, 0);
   std::vector<char> active(B, 1), stalled(B, 0);
@@ -232,6 +324,7 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
   for (auto &x : passes) ++x;
   TK_TRY(s.fetch(s.w.F, F));
   TK_TRY(s.fetch(s.w.gn2, gn2));
+  for (int64_t b = 0; b < B; ++b) best_gn2[b] = gn2[b];
 
   for (int it = 0; it < O->max_iter; ++it) {
     bool any = false;
@@ -255,8 +348,12 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
         cg[b] = active[b];
         eta[b] = std::min(0.5, sqrt(sqrt(gn2[b])));
       }
+      std::vector<int> list;
       for (int k = 0; k < max_cg; ++k) {
-        TK_TRY(s.hvp(A, s.w.d, s.w.Hd));
+        list.clear();
+        for (int64_t b = 0; b < B; ++b)
+          if (cg[b]) list.push_back((int)b);
+        TK_TRY(s.hvp_sub(list, A, s.w.d, s.w.Hd));
         for (int64_t b = 0; b < B; ++b) passes[b] += cg[b];
         TK_TRY(s.dots(s.w.d, s.w.Hd, dHd));
         for (int64_t b = 0; b < B; ++b) {
@@ -288,6 +385,12 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
       if (active[b] && !(slope[b] < 0)) {
         // not a descent direction (rounding in the inner solve): fall back to -grad
         slope[b] = -gn2[b];
+      } else if (active[b] && O->method == TK_NEWTON_CG && O->tol_rel_gap > 0 &&
+                 -0.5 * slope[b] <= O->tol_rel_gap * std::max(1.0, fabs(F[b]))) {
+        // Newton decrement: F - F* ~ -<g, p>/2 is below the relative tolerance
+        active[b] = 0;
+        status[b] = TK_OK;
+        stalled[b] = 1;  // stays finished
       }
     }
     // directions of problems whose slope was repaired: p = -g
@@ -298,27 +401,39 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
     // Armijo backtracking, all problems in lockstep
     std::vector<char> ls(B);
     std::vector<double> accepted(B, 0.0);
+    std::vector<char> real_decrease(B, 0);  // accepted by Armijo's test (a decrease F's rounding cannot fake)
     for (int64_t b = 0; b < B; ++b) ls[b] = active[b];
     for (int tries = 0; tries < 80; ++tries) {
       for (int64_t b = 0; b < B; ++b) {
         ca[b] = 1.0;
-        cb[b] = ls[b] ? t[b] : 0.0;
+        // problems that accepted a step keep it: the shared trial buffers
+        // (at, gt, Ft) must still hold their accepted point after the others'
+        // further trials
+        cb[b] = (ls[b] || accepted[b] != 0.0) ? t[b] : 0.0;
       }
       TK_TRY(s.axpby(ca, A, cb, s.w.p, s.w.at));
-      TK_TRY(s.objective(s.w.at, s.w.Ft, s.w.gt, s.w.gn2t));
+      std::vector<int> list;
+      for (int64_t b = 0; b < B; ++b)
+        if (ls[b]) list.push_back((int)b);
+      TK_TRY(s.objective_sub(list, s.w.at, s.w.Ft, s.w.gt, s.w.gn2t));
       TK_TRY(s.fetch(s.w.Ft, Ft));
       TK_TRY(s.fetch(s.w.gn2t, gn2t));
+      TK_TRY(s.dots(s.w.gt, s.w.p, slope_t));
       bool more = false;
       for (int64_t b = 0; b < B; ++b) {
         if (!ls[b]) continue;
         ++passes[b];
         // Armijo sufficient decrease; once the decrease is below the rounding
-        // level of F itself, a smaller gradient norm decides instead
+        // level of F itself, a smaller gradient norm decides instead; a
+        // non-positive slope at the trial point certifies decrease (F is
+        // convex along the line) when F's rounding hides it
         const bool armijo = Ft[b] <= F[b] + c_arm * t[b] * slope[b];
         const bool in_noise = fabs(Ft[b] - F[b]) <= 1e-12 * std::max(1.0, fabs(F[b])) && gn2t[b] < gn2[b];
-        if (armijo || in_noise) {
+        const bool downhill = slope_t[b] <= 0.0 && std::isfinite(Ft[b]);
+        if (armijo || in_noise || downhill) {
           ls[b] = 0;
           accepted[b] = 1.0;
+          real_decrease[b] = armijo && Ft[b] < F[b] - 1e-12 * std::max(1.0, fabs(F[b]));
         } else {
           t[b] *= 0.5;
           if (t[b] < 1e-30) {
@@ -341,6 +456,17 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
         F[b] = Ft[b];
         gn2[b] = gn2t[b];
         gstep[b] = t[b];
+      }
+      if (active[b] && !stalled[b]) {
+        // progress: a decrease of F beyond its rounding level, or |grad| below
+        // 0.999 of its best (the damped phase may raise |grad| while F falls)
+        const bool better_g = gn2[b] < 0.998 * best_gn2[b];
+        if (better_g) best_gn2[b] = gn2[b];
+        if (better_g || real_decrease[b]) {
+          since_best[b] = 0;
+        } else if (++since_best[b] >= kStallIters) {
+          stalled[b] = 1;  // the rounding floor of the contraction: no further progress
+        }
       }
     }
   }

@@ -5,7 +5,7 @@ import torch
 
 import oracle
 import synth
-from gpu_util import as_f64, contraction_bound, round_storage
+from gpu_util import as_f64, batched_bound, round_storage
 
 pytestmark = pytest.mark.gpu
 
@@ -28,9 +28,9 @@ def test_batched_contraction_matches_oracle(m, n, d, B, storage):
         g_ref, S_ref = oracle.contract(Kr, A[b], m)
         g_abs, S_abs = oracle.contract(np.abs(Kr), np.abs(A[b]), m)
         # the batched kernel flushes its FP32 accumulators every 2048 rows
-        tol = 4 * contraction_bound(max(n, 2048), g_abs, storage)
+        tol = 4 * batched_bound(g_abs, storage, n)
         assert np.all(np.abs(G[b] - g_ref) <= tol), (b, float(np.max(np.abs(G[b] - g_ref) / tol)))
-        assert abs(S[b] - S_ref) <= 4 * float(contraction_bound(max(n, 2048), np.array([S_abs]), storage)[0])
+        assert abs(S[b] - S_ref) <= 4 * float(batched_bound(np.array([S_abs]), storage, n)[0])
 
 
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
@@ -47,5 +47,5 @@ def test_batched_hvp_matches_oracle(m, n, d, B, storage):
     for b in sorted(set([0, B // 2, B - 1])):
         ref = oracle.hvp(Kr, A[b], V[b], m)
         hab = oracle.hvp(np.abs(Kr), np.abs(A[b]), np.abs(V[b]), m)
-        tol = 8 * contraction_bound(max(n, 2048), hab, storage)
+        tol = 8 * batched_bound(hab, storage, n)
         assert np.all(np.abs(HV[b] - ref) <= tol), (b, float(np.max(np.abs(HV[b] - ref) / tol)))

@@ -42,7 +42,7 @@ def test_contract_matches_oracle(m, n, d, storage):
         G, S = tk.tk_contract(Kd, m, n, A)
         torch.cuda.synchronize()
         g = G.double().cpu().numpy()
-        tol = contraction_bound(n, g_abs, storage)
+        tol = contraction_bound(n, g_abs, storage, m)
         if vdt == torch.float32:
             tol = tol + 2.0 ** -24 * np.abs(g_ref)  # output rounded to FP32
         err = np.abs(g - g_ref)
@@ -51,7 +51,7 @@ def test_contract_matches_oracle(m, n, d, storage):
             # the stated FP64 target: relative 1e-10
             assert np.allclose(g, g_ref, rtol=1e-10, atol=1e-10 * np.max(np.abs(g_ref)))
             assert float(S[0]) == pytest.approx(S_ref, rel=1e-10, abs=1e-10 * S_abs)
-        assert abs(float(S[0]) - S_ref) <= float(contraction_bound(n, np.array([S_abs]), storage)[0])
+        assert abs(float(S[0]) - S_ref) <= float(contraction_bound(n, np.array([S_abs]), storage, m)[0])
     assert tk.tk_status_read(tk.workspace(m, n)) == 0
 
 
@@ -67,7 +67,7 @@ def test_hvp_matches_oracle(m, n, d, storage):
     V = torch.tensor(v, device="cuda")
     HV, _ = tk.tk_contract(Kd, m, n, A, r=m - 2, V=V)
     hv = HV.cpu().numpy()
-    tol = 2 * contraction_bound(n, hv_abs, storage)
+    tol = 2 * contraction_bound(n, hv_abs, storage, m, dual=True)
     assert np.all(np.abs(hv - hv_ref) <= tol), np.max(np.abs(hv - hv_ref) / tol)
 
 
@@ -85,12 +85,12 @@ def test_batch_and_objective(storage):
     for b in range(B):
         g_ref, S_ref = oracle.contract(Kr, A[b], m)
         g_abs, S_abs = oracle.contract(np.abs(Kr), np.abs(A[b]), m)
-        tol = contraction_bound(n, g_abs, storage)
+        tol = contraction_bound(n, g_abs, storage, m)
         assert np.all(np.abs(G[b].cpu().numpy() - g_ref) <= tol)
         F_ref = oracle.dual_objective(S_ref, A[b], y, lam[b], m)
         gr_ref = oracle.dual_gradient(g_ref, A[b], y, lam[b])
         assert np.all(np.abs(grad[b].cpu().numpy() - gr_ref) <= tol + 1e-13 * np.abs(gr_ref))
-        assert float(F[b]) == pytest.approx(F_ref, abs=float(contraction_bound(n, np.array([S_abs]), storage)[0]) / m + 1e-12 * abs(F_ref))
+        assert float(F[b]) == pytest.approx(F_ref, abs=float(contraction_bound(n, np.array([S_abs]), storage, m)[0]) / m + 1e-12 * abs(F_ref))
         assert float(gn[b]) == pytest.approx(np.linalg.norm(gr_ref), abs=np.linalg.norm(tol) + 1e-12)
 
 
@@ -109,12 +109,12 @@ def test_range_shards_add_up(storage):
         g, s = tk.tk_contract(Kpart, m, n, A, off_lo=lo, off_hi=hi)
         g_ref, s_ref = oracle.contract(Kr[lo:hi], a, m, lo=lo)
         g_abs, _ = oracle.contract(np.abs(Kr[lo:hi]), np.abs(a), m, lo=lo)
-        assert np.all(np.abs(g.cpu().numpy() - g_ref) <= contraction_bound(n, g_abs, storage))
+        assert np.all(np.abs(g.cpu().numpy() - g_ref) <= contraction_bound(n, g_abs, storage, m, lo, hi))
         G += g
         S += float(s[0])
     g_ref, S_ref = oracle.contract(Kr, a, m)
     g_abs, S_abs = oracle.contract(np.abs(Kr), np.abs(a), m)
-    assert np.all(np.abs(G.cpu().numpy() - g_ref) <= 4 * contraction_bound(n, g_abs, storage))
+    assert np.all(np.abs(G.cpu().numpy() - g_ref) <= 4 * contraction_bound(n, g_abs, storage, m))
 
 
 def test_rejects_bad_arguments():

@@ -8,7 +8,7 @@ import torch
 
 import oracle
 import synth
-from gpu_util import U32, UBF16, as_f64
+from gpu_util import U32, UBF16, accumulation_depth, as_f64, max_warp_triangles
 
 pytestmark = pytest.mark.gpu
 
@@ -66,7 +66,7 @@ def test_contraction_closed_form(built):
         g_abs = np.abs(X) @ uabs ** (m - 1)
         S_abs = float(np.sum(uabs ** m))
         # storage rounding + build accumulation + contraction accumulation
-        k = (d + m + 2) + (2 * n + 64)
+        k = (d + m + 2) + accumulation_depth(n, max_warp_triangles(m, n, storage))
         rel = 1.01 * (U[storage] + k * U32) if storage == "bf16" else 1.01 * k * U32
         err = np.abs(G.cpu().numpy() - g_ref)
         assert np.all(err <= rel * g_abs), float(np.max(err / (rel * g_abs)))
@@ -84,7 +84,7 @@ def test_hvp_closed_form(built):
     hv_ref = X @ (u ** (m - 2) * (X.T @ v))
     uabs = np.abs(X).T @ np.abs(a)
     hv_abs = np.abs(X) @ (uabs ** (m - 2) * (np.abs(X).T @ np.abs(v)))
-    k = (d + m + 2) + 2 * (2 * n + 64)
+    k = (d + m + 2) + 2 * accumulation_depth(n, max_warp_triangles(m, n, storage, dual=True))
     rel = 1.01 * (U[storage] + k * U32) if storage == "bf16" else 1.01 * k * U32
     err = np.abs(HV.cpu().numpy() - hv_ref)
     assert np.all(err <= rel * hv_abs), float(np.max(err / (rel * hv_abs)))

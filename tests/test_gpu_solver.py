@@ -99,3 +99,43 @@ def test_gradient_descent_method():
     assert rc == tk.TK_OK, rep
     a_ref, info = oracle.solve_dual_newton(oracle.build(X, m), y, lam, m, tol=1e-12)
     assert np.linalg.norm(A[0].cpu().numpy() - a_ref) <= (1e-8 + info["gradnorm"]) / lam + 1e-12
+
+
+def test_batch_solves_each_problem_as_alone():
+    # The line search runs in lockstep over the batch: a problem that accepts
+    # its step while another still backtracks must keep it (and a compacted
+    # pass over the problems still searching must not disturb it).  With FP64
+    # storage a batch does, problem by problem, the arithmetic of a solve of
+    # that problem alone, up to the rounding of kernels that differ between the
+    # full and the compacted passes.
+    m, n, d = 4, 26, 4
+    X = synth.small_problem(m, n, d, salt=61)
+    y = X @ synth.thesis_weights(synth.rng_for(8), d, 2) + 0.05 * synth.alpha_like(n, salt=62)
+    lams = np.array([1e-2, 10.0, 0.3])  # the small lambda backtracks, the large one does not
+    K = tk.tk_build_packed(torch.tensor(X, device="cuda"), m, storage="f64")
+    yt = torch.tensor(y, device="cuda")
+    for it in (1, 2, 3):
+        A, rep, _ = tk.tk_solve_dual(K, m, n, yt, lams, tol=1e-10, max_iter=it)
+        for b in range(3):
+            A1, rep1, _ = tk.tk_solve_dual(K, m, n, yt, lams[b:b + 1], tol=1e-10, max_iter=it)
+            assert rep1[0]["passes"] == rep[b]["passes"]
+            assert np.allclose(A[b].cpu().numpy(), A1[0].cpu().numpy(), rtol=1e-12, atol=1e-13), (it, b)
+    A, rep, rc = tk.tk_solve_dual(K, m, n, yt, lams, tol=1e-10)
+    assert rc == tk.TK_OK
+    for b in range(3):
+        A1, rep1, rc1 = tk.tk_solve_dual(K, m, n, yt, lams[b:b + 1], tol=1e-10)
+        assert rc1 == tk.TK_OK
+        dist = float((A[b] - A1[0]).norm())
+        assert dist <= (rep[b]["gradnorm"] + rep1[0]["gradnorm"]) / lams[b] + 1e-12
+
+
+def test_relative_gap_stop():
+    # Newton decrement stop: F - F* ~ -<grad F, p>/2 <= rel_gap max(1, |F|)
+    p = synth.plain_fp64()
+    m, X, y, lam = p["m"], p["X"], p["y"], p["lam"]
+    n = X.shape[0]
+    K = tk.tk_build_packed(torch.tensor(X, device="cuda"), m, storage="f64")
+    A, rep, rc = tk.tk_solve_dual(K, m, n, torch.tensor(y, device="cuda"), [lam], tol=0.0, rel_gap=1e-8)
+    assert rc == tk.TK_OK and rep[0]["status"] == tk.TK_OK
+    a_ref, info = oracle.solve_dual_newton(oracle.build(X, m), y, lam, m, tol=1e-12)
+    assert abs(rep[0]["F"] - info["F"]) <= 1e-7 * max(1.0, abs(info["F"]))

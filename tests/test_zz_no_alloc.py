@@ -34,10 +34,10 @@ def test_noalloc_matches_contract(m, n, d, storage, vdt):
     g_ref = G_ref.double().cpu().numpy()
     # both results carry the contraction's accumulation error; the outputs
     # are rounded to the vector type
-    tol = 2 * contraction_bound(n, g_abs, storage)
+    tol = 2 * contraction_bound(n, g_abs, storage, m)
     if vdt == torch.float32:
         tol = tol + 2 * U32 * np.abs(g_ref)
-    s_tol = 2 * float(contraction_bound(n, np.array([S_abs]), storage)[0])
+    s_tol = 2 * float(contraction_bound(n, np.array([S_abs]), storage, m)[0])
     for _ in range(2):
         G = torch.full((n,), float("nan"), dtype=vdt, device="cuda")
         S = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
