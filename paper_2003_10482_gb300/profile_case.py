@@ -1,0 +1,67 @@
+"""Small, repeatable launches of one kernel, for profiler captures.
+
+    python -m paper_2003_10482_gb300.profile_case contract --m 4 --n 350 --storage f32 --reps 5
+    python -m paper_2003_10482_gb300.profile_case batched --m 4 --n 300 --B 512 --reps 3
+    python -m paper_2003_10482_gb300.profile_case build --m 4 --n 300 --d 80 --reps 2
+
+Inputs are the seeded synthetic ones of the benchmarks (X ~ U(-1, 1) rows of
+the full FP32 workload, or N(0, 1) rows of the batched workload's points);
+each case builds its packed tensor once, then launches the kernel `--reps`
+times (the first launches are warm-up for `ncu -s`).  Prints the mean
+CUDA-event time per launch.
+"""
+from __future__ import annotations
+
+import argparse
+
+import torch
+
+import paper_2003_10482_gb300 as tk
+import synth
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["contract", "hvp", "batched", "batched_hvp", "build"])
+    ap.add_argument("--m", type=int, default=4)
+    ap.add_argument("--n", type=int, default=300)
+    ap.add_argument("--d", type=int, default=80)
+    ap.add_argument("--B", type=int, default=512)
+    ap.add_argument("--storage", default="f32", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--reps", type=int, default=3)
+    args = ap.parse_args()
+    torch.cuda.set_device(0)
+    if args.case in ("contract", "hvp"):
+        X = synth.full_fp32()["X"][: args.n]
+    else:
+        X = synth.batched_path()["X"][: args.n, : args.d]
+    Xd = torch.tensor(X, device="cuda")
+    m, n = args.m, Xd.shape[0]
+    K = tk.tk_build_packed(Xd, m, storage=args.storage)
+    B = 1 if args.case in ("contract", "hvp") else args.B
+    A = torch.tensor(synth.alpha_like(n, salt=1, batch=B), device="cuda")
+    V = torch.tensor(synth.alpha_like(n, salt=2, batch=B), device="cuda")
+    ws = tk.workspace(m, n, B)
+    if args.case == "build":
+        def run():
+            tk.tk_build_packed(Xd, m, storage=args.storage)
+    elif args.case in ("contract", "batched"):
+        def run():
+            tk.tk_contract(K, m, n, A, work=ws)
+    else:
+        def run():
+            tk.tk_contract(K, m, n, A, r=m - 2, V=V, work=ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.reps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.reps
+    print(f"{args.case} m={m} n={n} B={B} {args.storage}: {ms:.3f} ms per launch "
+          f"({K.numel():,} packed entries, status {tk.tk_status_read(ws)})")
+
+
+if __name__ == "__main__":
+    main()
