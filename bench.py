@@ -230,6 +230,11 @@ def batched_leg(dev) -> dict:
     K32 = tk.tk_build_packed(X, m, storage="f32")
     K64 = tk.tk_build_packed(X, m, storage="f64")
     gap, iters = 1e-7, 40
+    # batch width per lane, staging tile, buffers, slices and the batched /
+    # single-vector crossover, chosen by measurement on the Hessian-vector
+    # product (most passes of a Newton-CG solve are HVPs); untimed
+    from paper_2003_10482_gb300 import autotune
+    tuned = autotune.tune_batched(K32, m, n, int(lam.numel()), dual=True, reps=2)
     tk.tk_solve_dual(K32, m, n, y, lam[:32], mask=mask[:32], tol=0.0, rel_gap=gap, max_iter=2)  # warm-up
     tk.tk_solve_dual(K64, m, n, y, lam[:1], mask=mask[:1], tol=0.0, rel_gap=gap, max_iter=2)
     torch.cuda.synchronize()
@@ -254,6 +259,7 @@ def batched_leg(dev) -> dict:
                            "batched_passes": rep[j]["passes"]})
     held_out = float(A32[~mask.bool()].abs().max()) if bool((~mask.bool()).any()) else 0.0
     plain_s = statistics.mean(t_plain)
+    tk.tk_batched_set_config(reset=True)
     return {"workload": "batched_path_m4_np300_d80 (lambda in [0.27, 1] x 8 folds)", "problems": B,
             "batched_fp32": {"solves_per_s": B / t_batched, "seconds": t_batched,
                              "converged": sum(r["status"] == 0 for r in rep),
@@ -261,6 +267,7 @@ def batched_leg(dev) -> dict:
             "plain_fp64": {"solves_per_s": 1.0 / plain_s, "seconds_per_solve": plain_s, "timed_problems": len(sample)},
             "speedup": (B / t_batched) * plain_s,
             "target": "relative objective gap 1e-7 (Newton decrement), at most 40 Newton iterations",
+            "autotuned": {"config": tuned["best"], "hvp_ms": tuned["ms"], "candidates": len(tuned["trials"])},
             "max_rel_obj_diff_vs_fp64": max(errs), "held_out_max_abs_alpha": held_out,
             "per_lambda": per_lambda}
 

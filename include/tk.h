@@ -189,6 +189,32 @@ int tk_contract_set_config(const tk_contract_config *cfg);
  * under the current settings (dual != 0: the HVP variant). */
 int tk_contract_get_config(int m, int64_t n, int storage_dtype, int dual, tk_contract_config *out);
 
+/* Launch configuration of the batched contraction (B vectors per pass).  Zero
+ * fields keep the library's choice.
+ *   vpl          vectors per lane (1 or 2): a block serves 32 * vpl vectors
+ *   block_bytes  bytes of one staging buffer (a multiple of 128 in [4096, 65536])
+ *   nbuf         staging buffers per block, 2..4
+ *   slice_mult   blocks per group of vectors = slice_mult * SMs / groups (1 or 2)
+ *   min_batch    smallest B that takes the batched kernel (below it the
+ *                single-vector pass runs once per vector); 0 = 28 (16 for
+ *                r = m-2); a value sets both */
+typedef struct {
+    int vpl;
+    int block_bytes;
+    int nbuf;
+    int slice_mult;
+    int min_batch;
+} tk_batched_config;
+
+/* Sets the process-wide batched configuration (NULL restores the defaults).
+ * Used by the autotuner; not thread-safe against concurrent contractions. */
+int tk_batched_set_config(const tk_batched_config *cfg);
+
+/* The configuration a batched contraction of (m, n, storage_dtype, B) would
+ * launch with under the current settings (dual != 0: r = m-2).  vpl = 0 in
+ * the result means the batched kernel does not cover the shape. */
+int tk_batched_get_config(int m, int64_t n, int storage_dtype, int dual, int64_t B, tk_batched_config *out);
+
 /* Host-only: the row-aligned cut of [off_lo, off_hi) into `pieces` consecutive
  * pieces of near-equal cost (entries + row_cost per row + tri_cost per
  * triangle entered), as the contraction assigns them to warps.

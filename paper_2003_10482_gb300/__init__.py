@@ -74,6 +74,8 @@ def _declare(L):
         "tk_status_read": (i32, [P, P]),
         "tk_contract_set_config": (i32, [P]),
         "tk_contract_get_config": (i32, [i32, i64, i32, i32, P]),
+        "tk_batched_set_config": (i32, [P]),
+        "tk_batched_get_config": (i32, [i32, i64, i32, i32, i64, P]),
         "tk_contract_plan": (i32, [i32, i64, i64, i64, i32, i32, i32, P]),
         "tk_objective": (i32, [i32, i64, i32, P, i64, P, P, P, P, P, P, P, sz, P]),
         "tk_assemble_objective": (i32, [i32, i64, i64, P, P, P, P, P, P, P, P, P]),
@@ -206,6 +208,27 @@ def tk_contract_plan(m: int, n: int, off_lo: int, off_hi: int, pieces: int, row_
 def tk_contract_get_config(m: int, n: int, storage="f32", dual: bool = False) -> dict:
     c = tk_contract_config()
     _check(lib().tk_contract_get_config(m, n, dtype_code(storage), int(dual), ctypes.byref(c)))
+    return {f: getattr(c, f) for f, _ in c._fields_}
+
+
+class tk_batched_config(ctypes.Structure):
+    _fields_ = [("vpl", ctypes.c_int), ("block_bytes", ctypes.c_int), ("nbuf", ctypes.c_int),
+                ("slice_mult", ctypes.c_int), ("min_batch", ctypes.c_int)]
+
+
+def tk_batched_set_config(vpl=0, block_bytes=0, nbuf=0, slice_mult=0, min_batch=0, reset=False):
+    """Process-wide launch configuration of the batched contraction (0 = library choice)."""
+    if reset:
+        _check(lib().tk_batched_set_config(None))
+        return
+    c = tk_batched_config(vpl, block_bytes, nbuf, slice_mult, min_batch)
+    _check(lib().tk_batched_set_config(ctypes.byref(c)))
+
+
+def tk_batched_get_config(m: int, n: int, storage="f32", dual: bool = False, B: int = 512) -> dict:
+    """The batched launch a contraction of B vectors would use (vpl 0: not covered)."""
+    c = tk_batched_config()
+    _check(lib().tk_batched_get_config(m, n, dtype_code(storage), int(dual), B, ctypes.byref(c)))
     return {f: getattr(c, f) for f, _ in c._fields_}
 
 

@@ -169,8 +169,7 @@ static int contract_impl(int m, int64_t n, int storage, const void *K, int64_t o
   // for one vector as for 64 (32 for the HVP), while the single-vector kernel
   // runs at the HBM rate (measured on GB300, m = 4, n = 300: the batched
   // kernel wins from B = 28 for K[a^{m-1}] and from B = 16 for the HVP).
-  const int64_t min_batched = (r == m - 2) ? 16 : 28;
-  if (B >= min_batched && storage != TK_F64) {
+  if (B >= batched_min_batch(r == m - 2) && storage != TK_F64) {
     BatchedArgs ba;
     ba.m = m;
     ba.n = (int)n;
@@ -266,6 +265,33 @@ int tk_contract_get_config(int m, int64_t n, int storage, int dual, tk_contract_
   if (storage < TK_F64 || storage > TK_BF16) return fail(TK_EINVAL, "bad storage dtype %d", storage);
   int grid = 0;
   return contract_resolve(m, (int)n, storage, dual != 0, out, &grid);
+}
+
+int tk_batched_set_config(const tk_batched_config *cfg) {
+  if (!cfg) {
+    g_batched_cfg = tk_batched_config{0, 0, 0, 0, 0};
+    return TK_OK;
+  }
+  if (cfg->vpl < 0 || cfg->vpl > 2 ||
+      (cfg->block_bytes != 0 && (cfg->block_bytes < 4096 || cfg->block_bytes > 65536 || cfg->block_bytes % 128)) ||
+      (cfg->nbuf != 0 && (cfg->nbuf < 2 || cfg->nbuf > 4)) || cfg->slice_mult < 0 || cfg->slice_mult > 2 ||
+      cfg->min_batch < 0)
+    return fail(TK_EINVAL, "batched config out of range");
+  g_batched_cfg = *cfg;
+  return TK_OK;
+}
+
+int tk_batched_get_config(int m, int64_t n, int storage, int dual, int64_t B, tk_batched_config *out) {
+  if (!out) return fail(TK_EINVAL, "NULL output");
+  int rc = check_order_points(m, n);
+  if (rc != TK_OK) return rc;
+  if (storage < TK_F64 || storage > TK_BF16) return fail(TK_EINVAL, "bad storage dtype %d", storage);
+  if (B < 1) return fail(TK_EINVAL, "B < 1");
+  DevInfo di;
+  rc = dev_info(&di);
+  if (rc != TK_OK) return rc;
+  batched_resolve((int)n, storage, dual != 0, B, di.sms, di.smem_optin, out);
+  return TK_OK;
 }
 
 int tk_status_read(void *work, void *stream) {

@@ -587,19 +587,58 @@ size_t batched_workspace_bytes(int n, int64_t B, int sms) {
   return sizeof(WsHeader) + (size_t)16 * sms * sizeof(WarpPlan) + (size_t)blocks * 2 * (n + 2) * 64 * sizeof(double);
 }
 
+tk_batched_config g_batched_cfg = {0, 0, 0, 0, 0};
+
+int64_t batched_min_batch(bool dual) {
+  return g_batched_cfg.min_batch > 0 ? g_batched_cfg.min_batch : (dual ? 16 : 28);
+}
+
+static size_t batched_smem(int n, bool dual, int vpl, int nbuf, int buf_bytes) {
+  const int BL = 32 * vpl, nv = dual ? 2 : 1;
+  const size_t vec_bytes = ((size_t)nv * n * BL * 4 + 127) & ~size_t(127);
+  const size_t fixed = (size_t)(kBW * 16 * BL * nv + 2 * kBW * BL * nv + 2 * BL * nv) * 4 + (size_t)BL * nv * 8 +
+                       64 + 64 + 128;
+  return vec_bytes + fixed + (size_t)nbuf * buf_bytes;
+}
+
+bool batched_resolve(int n, int storage, bool dual, int64_t B, int sms, int smem_optin, tk_batched_config *out) {
+  const tk_batched_config &o = g_batched_cfg;
+  *out = tk_batched_config{0, 0, 0, 0, (int)batched_min_batch(dual)};
+  if (storage == TK_F64) return false;
+  int vpl = 0, ncol = 0;
+  if (!batched_shape(n, dual, &vpl, &ncol)) return false;
+  if (o.vpl == 1) vpl = 1;  // vpl 2 only where the shape allows it
+  const int es = dtype_size(storage);
+  const int min_buf = (n * es + 32 + 127) & ~127;
+  int buf = o.block_bytes > 0 ? o.block_bytes : std::max(8192 + 128, min_buf);
+  if (buf < min_buf) return false;
+  const int nbuf = o.nbuf > 0 ? o.nbuf : 3;
+  const int BL = 32 * vpl;
+  const int64_t groups = (B + BL - 1) / BL;
+  if (groups > (int64_t)sms * 2) return false;
+  if (batched_smem(n, dual, vpl, nbuf, buf) > (size_t)smem_optin - 1024) return false;
+  out->vpl = vpl;
+  out->block_bytes = buf;
+  out->nbuf = nbuf;
+  out->slice_mult = o.slice_mult > 0 ? o.slice_mult : 1;
+  return true;
+}
+
 int contract_batched(const BatchedArgs &a, cudaStream_t st) {
   const bool dual = a.V != nullptr;
   if (a.storage == TK_F64) return fail(TK_EUNSUPPORTED, "batched kernel stores FP32/BF16");
-  int vpl = 0, ncol = 0;
-  if (!batched_shape(a.n, dual, &vpl, &ncol)) return fail(TK_EUNSUPPORTED, "batched kernel: n too large");
   DevInfo di;
   int rc = dev_info(&di);
   if (rc != TK_OK) return rc;
+  tk_batched_config cfg;
+  if (!batched_resolve(a.n, a.storage, dual, a.B, di.sms, di.smem_optin, &cfg))
+    return fail(TK_EUNSUPPORTED, "batched kernel does not cover this shape or configuration");
+  int vpl = 0, ncol = 0;
+  batched_shape(a.n, dual, &vpl, &ncol);
+  vpl = cfg.vpl;
   const int BL = 32 * vpl;
-  const int64_t groups64 = (a.B + BL - 1) / BL;
-  if (groups64 > (int64_t)di.sms * 2) return fail(TK_EUNSUPPORTED, "batched kernel: B too large for one launch");
-  const int groups = (int)groups64;
-  const int slices = std::max(1, di.sms / groups);
+  const int groups = (int)((a.B + BL - 1) / BL);
+  const int slices = std::max(1, cfg.slice_mult * di.sms / groups);
   const int grid = groups * slices;
   const int es = dtype_size(a.storage);
   const int nv = dual ? 2 : 1;
@@ -617,17 +656,12 @@ int contract_batched(const BatchedArgs &a, cudaStream_t st) {
   bp.groups = groups;
   bp.slices = slices;
   bp.pieces = 16 * slices;
-  bp.nbuf = 3;
-  int bl = 13;
-  while ((1 << bl) < a.n * es) ++bl;
-  bp.cap = (1 << bl) / es;
-  bp.buf_bytes = (((1 << bl) + 32) + 127) & ~127;
+  bp.nbuf = cfg.nbuf;
+  bp.buf_bytes = cfg.block_bytes;
+  bp.cap = (cfg.block_bytes - 32) / es;
   bp.flush_rows = 2048;
   bp.vec_bytes = (int)(((size_t)nv * a.n * BL * 4 + 127) & ~size_t(127));
-  const size_t fixed = (size_t)(kBW * 16 * BL * nv + 2 * kBW * BL * nv + 2 * BL * nv) * 4 + (size_t)BL * nv * 8 +
-                       64 + 64 + 128;
-  const size_t smem = bp.vec_bytes + fixed + (size_t)bp.nbuf * bp.buf_bytes;
-  if (smem > (size_t)di.smem_optin - 1024) return fail(TK_EUNSUPPORTED, "batched kernel: shared memory");
+  const size_t smem = batched_smem(a.n, dual, vpl, bp.nbuf, bp.buf_bytes);
   unsigned char *ws = reinterpret_cast<unsigned char *>(a.work);
   const size_t plan_bytes = (size_t)16 * di.sms * sizeof(WarpPlan);
   const size_t part_bytes = (size_t)grid * 2 * (a.n + 2) * BL * sizeof(double);

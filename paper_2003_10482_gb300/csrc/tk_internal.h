@@ -63,6 +63,10 @@ struct BatchedArgs {
   size_t work_bytes;
 };
 int contract_batched(const BatchedArgs &a, cudaStream_t st);
+extern tk_batched_config g_batched_cfg;
+// resolved batched launch shape; returns false when the kernel does not cover it
+bool batched_resolve(int n, int storage, bool dual, int64_t B, int sms, int smem_optin, tk_batched_config *out);
+int64_t batched_min_batch(bool dual);
 size_t batched_workspace_bytes(int n, int64_t B, int sms);
 
 // Device properties cached per device.

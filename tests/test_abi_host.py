@@ -118,3 +118,13 @@ def test_nystrom_select_matches_oracle(L, N, np_, seed):
 def test_nystrom_select_rejects_bad_sizes(L):
     with pytest.raises(tk.TKError):
         tk.tk_nystrom_select(5, 6, 1)
+
+
+def test_batched_config_validation():
+    tk = pytest.importorskip("paper_2003_10482_gb300")
+    for bad in (dict(vpl=3), dict(block_bytes=1000), dict(block_bytes=4100), dict(nbuf=5), dict(slice_mult=3),
+                dict(min_batch=-1)):
+        with pytest.raises(tk.TKError):
+            tk.tk_batched_set_config(**bad)
+    tk.tk_batched_set_config(vpl=1, block_bytes=8320, nbuf=2, slice_mult=2, min_batch=4)
+    tk.tk_batched_set_config(reset=True)
