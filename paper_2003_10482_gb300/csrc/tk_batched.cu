@@ -579,12 +579,15 @@ static bool batched_shape(int n, bool dual, int *vpl, int *ncol) {
   return false;
 }
 
+// plan records: 16 pieces per slice, slices <= slice_mult (<= 2) * SMs
+static size_t batched_plan_bytes(int sms) { return (size_t)16 * 2 * sms * sizeof(WarpPlan); }
+
 size_t batched_workspace_bytes(int n, int64_t B, int sms) {
-  // header, plan (16 pieces per slice, at most one slice per SM), partials
+  // header, plan (16 pieces per slice, at most two slices per SM), partials
   const int BL = 32;  // the smallest group gives the most blocks
   const int64_t groups = (B + BL - 1) / BL;
   const int64_t blocks = std::max<int64_t>(groups, (int64_t)sms) * 2;
-  return sizeof(WsHeader) + (size_t)16 * sms * sizeof(WarpPlan) + (size_t)blocks * 2 * (n + 2) * 64 * sizeof(double);
+  return sizeof(WsHeader) + batched_plan_bytes(sms) + (size_t)blocks * 2 * (n + 2) * 64 * sizeof(double);
 }
 
 tk_batched_config g_batched_cfg = {0, 0, 0, 0, 0};
@@ -663,7 +666,9 @@ int contract_batched(const BatchedArgs &a, cudaStream_t st) {
   bp.vec_bytes = (int)(((size_t)nv * a.n * BL * 4 + 127) & ~size_t(127));
   const size_t smem = batched_smem(a.n, dual, vpl, bp.nbuf, bp.buf_bytes);
   unsigned char *ws = reinterpret_cast<unsigned char *>(a.work);
-  const size_t plan_bytes = (size_t)16 * di.sms * sizeof(WarpPlan);
+  const size_t plan_bytes = batched_plan_bytes(di.sms);
+  if ((size_t)bp.pieces * sizeof(WarpPlan) > plan_bytes)
+    return fail(TK_EINVAL, "batched plan of %d pieces exceeds its workspace region", bp.pieces);
   const size_t part_bytes = (size_t)grid * 2 * (a.n + 2) * BL * sizeof(double);
   if (sizeof(WsHeader) + plan_bytes + part_bytes > a.work_bytes) return fail(TK_ENOMEM, "batched workspace too small");
   WarpPlan *plan = reinterpret_cast<WarpPlan *>(ws + sizeof(WsHeader));
