@@ -194,6 +194,12 @@ __device__ __forceinline__ CT ld_vec(const void *p, int dt, int i) {
 }
 
 
+// 1/k for k = 0..15 (entry 0 unused), each the correctly rounded quotient
+template <typename CT>
+__device__ constexpr CT kInvSmall[16] = {CT(0),      CT(1) / 1,  CT(1) / 2,  CT(1) / 3,  CT(1) / 4,  CT(1) / 5,
+                                         CT(1) / 6,  CT(1) / 7,  CT(1) / 8,  CT(1) / 9,  CT(1) / 10, CT(1) / 11,
+                                         CT(1) / 12, CT(1) / 13, CT(1) / 14, CT(1) / 15};
+
 constexpr int kRB = 16;    // rows per block of the batched kernel (upper bound)
 constexpr int kRows = 32;  // rows per block of the single-vector kernel (upper bound)
 
@@ -272,7 +278,10 @@ __device__ __forceinline__ int block_rows(int n, int c, int64_t pos, int64_t end
 // holds, in xc[i], the entry of row i at column d = n-1-(32K+j) (loaded one
 // step earlier), adds it into g_d's accumulator and into row i's dot; before
 // that it issues the loads of chunk K-1 into xn[] (zero past a row's end when
-// MASKN, so the multiply-adds need no masks).
+// MASKN, so the multiply-adds need no masks).  MASKN is set only when chunk
+// K-1 is the second-highest chunk T-2 of the quad (T = ceil(sl_0 / 32)):
+// sl_0 > 32 (T-1) and sl_1 = sl_0 - 1 >= 32 (T-1), so rows 0 and 1 hold every
+// column of that chunk and only rows 2 and 3 can end inside it.
 template <int K, bool MASKN, int NC, typename ST, typename CT, bool D>
 __device__ __forceinline__ void quad_step(Nm<CT, D> (&acc)[NC], Nm<CT, D> (&dot)[4], const Nm<CT, D> (&ar)[NC],
                                           const ST *const (&prow)[4], const int (&sl)[4], int lane,
@@ -280,7 +289,7 @@ __device__ __forceinline__ void quad_step(Nm<CT, D> (&acc)[NC], Nm<CT, D> (&dot)
   if constexpr (K >= 1 && K - 1 < NC) {
 #pragma unroll
     for (int i = 0; i < 4; ++i)
-      xn[i] = (!MASKN || 32 * (K - 1) + lane < sl[i]) ? ld_elem<ST, CT>(prow[i] - 32 * (K - 1)) : CT(0);
+      xn[i] = (!MASKN || i < 2 || 32 * (K - 1) + lane < sl[i]) ? ld_elem<ST, CT>(prow[i] - 32 * (K - 1)) : CT(0);
   }
   if constexpr (K < NC) {
 #pragma unroll
@@ -551,25 +560,23 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
 
   auto setup_triangle = [&]() {
     AQ = mk<CT, D>(CT(1), CT(0));
-    int fact_m = 1;
-    for (int i = 2; i <= m; ++i) fact_m *= i;
-    int den = 1, run = 0;
+    // M' = m! / prod_v cnt_Q(v)!: divide m! by the position of each entry in
+    // its run of equal values (every partial quotient is a multinomial
+    // coefficient, so each division is exact)
+    uint64_t mp = 1;
+    for (int i = 2; i <= m; ++i) mp *= (uint64_t)i;
+    int run = 0;
     for (int j = 0; j < m - 2; ++j) {
       AQ = AQ * alpha_at(Q[j]);
       run = (j > 0 && Q[j] == Q[j - 1]) ? run + 1 : 1;
-      den *= run;  // accumulates prod_v cnt_Q(v)!
+      if (run > 1) mp = exact_div_small(mp, run);
     }
-    if (m > 2) {
-      b = Q[m - 3];
-      kb = 0;
-      for (int j = 0; j < m - 2; ++j) kb += (Q[j] == b);
-    } else {
-      b = -1;
-      kb = 0;
-    }
-    Mprime = CT(fact_m / den);
-    Mf = Mprime / CT(kb + 1);
-    inv_first = CT(1) / CT(kb + 2);
+    // the last run is the one of b = Q[m-3]: its length is cnt_Q(b)
+    b = (m > 2) ? Q[m - 3] : -1;
+    kb = (m > 2) ? run : 0;
+    Mprime = CT(mp);
+    Mf = CT(exact_div_small(mp, kb + 1));  // M' / (cnt_Q(b) + 1), an integer
+    inv_first = kInvSmall<CT>[kb + 2];      // 1 / (cnt_Q(b) + 2), cnt_Q(b) <= m - 2
     cA = scale(Mprime * inv_m, AQ);
     cAf = scale(Mf * inv_m, AQ);
   };
