@@ -229,9 +229,12 @@ struct KParams {
 
 // Threads per block the register budget allows: a base of ~64 registers plus
 // the per-lane column state (acc[] and alpha[], doubled for dual numbers and
-// for FP64).  Above 120 estimated registers the block is capped at 256 threads.
+// for FP64).  Up to 120 estimated registers: 512 threads (128 registers
+// each); up to 160: 384 threads (170 registers); above: 256 threads.
 __host__ __device__ constexpr int max_threads_est(int ct_bytes, bool dual, int nc) {
-  return (64 + (dual ? 2 : 1) * (ct_bytes / 4) * 2 * nc <= 120 && !(dual && ct_bytes == 8)) ? 512 : 256;
+  const int est = 64 + (dual ? 2 : 1) * (ct_bytes / 4) * 2 * nc;
+  if (dual && ct_bytes == 8) return 256;
+  return est <= 120 ? 512 : (est <= 160 ? 384 : 256);
 }
 template <typename CT, bool D, int NC>
 constexpr int max_threads() {
