@@ -262,6 +262,20 @@ int tk_objective(int m, int64_t n, int storage_dtype, const void *K, int64_t B,
                  double *grad, double *gnorm, void *work, size_t work_bytes,
                  void *stream);
 
+/* Bytes of workspace tk_objective_host needs for (m, n): the contraction's
+ * workspace plus device staging for the dual vector and the results. */
+size_t tk_objective_host_workspace_size(int m, int64_t n);
+
+/* tk_objective for one dual vector held in HOST memory, results back in HOST
+ * memory, in one call: copies A_host (n FP64) to the device, runs the pass,
+ * copies out_host[0] = F, out_host[1] = |grad F|_2, out_host[2..n+1] = grad F
+ * (n + 2 FP64) back and synchronises `stream`.  y and lambda (1 value) are
+ * device pointers.  Host buffers may be pageable; pinned ones let the copies
+ * run at full speed.  Returns after out_host is written. */
+int tk_objective_host(int m, int64_t n, int storage_dtype, const void *K, const double *A_host,
+                      const double *y, const double *lambda, double *out_host, void *work,
+                      size_t work_bytes, void *stream);
+
 /* Dual objective and gradient from contractions that were already reduced
  * (for instance summed over the shards of several devices):
  *   F[b] = S[b]/m + (lambda_b/2)|A_b|^2 - <y, A_b>,  grad[b] = G[b] + lambda_b A_b - y,

@@ -79,6 +79,8 @@ def _declare(L):
         "tk_contract_plan": (i32, [i32, i64, i64, i64, i32, i32, i32, P]),
         "tk_objective": (i32, [i32, i64, i32, P, i64, P, P, P, P, P, P, P, sz, P]),
         "tk_assemble_objective": (i32, [i32, i64, i64, P, P, P, P, P, P, P, P, P]),
+        "tk_objective_host_workspace_size": (sz, [i32, i64]),
+        "tk_objective_host": (i32, [i32, i64, i32, P, P, P, P, P, P, sz, P]),
         "tk_contract_noalloc": (i32, [i32, i64, i32, P, i32, P, P, P, P]),
         "tk_solve_workspace_size": (sz, [P]),
         "tk_primal": (i32, [i32, i64, i64, P, i64, P, P, P]),
@@ -312,6 +314,33 @@ def tk_objective(K: torch.Tensor, m: int, n: int, A: torch.Tensor, y: torch.Tens
                               _p(y.to(torch.float64).contiguous()), _p(lam_t), _p(F), _p(grad),
                               _p(gn), _p(work), work.numel(), _stream(stream)))
     return F, grad.reshape(A.shape), gn
+
+
+_host_ws: dict = {}
+
+
+def tk_objective_host(K: torch.Tensor, m: int, n: int, A_host: torch.Tensor, y: torch.Tensor, lam: torch.Tensor,
+                      out_host: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """The dual objective of one dual vector in host memory, results in host
+    memory, in one C-ABI call (host -> device copy, pass, device -> host copy,
+    stream synchronisation).  A_host: (n,) FP64 CPU tensor (pinned for speed);
+    y, lam: device tensors.  Returns out_host = [F, |grad F|, grad F...] ((n+2,) FP64 CPU)."""
+    if A_host.device.type != "cpu" or A_host.dtype != torch.float64 or not A_host.is_contiguous():
+        raise TKError(TK_EINVAL, "A_host must be a contiguous FP64 CPU tensor")
+    if out_host is None:
+        out_host = torch.empty(n + 2, dtype=torch.float64, pin_memory=A_host.is_pinned())
+    dev = K.device
+    need = int(lib().tk_objective_host_workspace_size(m, n))
+    if need == 0:
+        raise TKError(TK_EINVAL, lib().tk_last_error().decode())
+    ws = _host_ws.get(dev.index)
+    if ws is None or ws.numel() < need:
+        ws = torch.zeros(need, dtype=torch.uint8, device=dev)
+        _host_ws[dev.index] = ws
+    _check(lib().tk_objective_host(m, n, dtype_code(K.dtype), _p(K), ctypes.c_void_p(A_host.data_ptr()),
+                                   _p(y), _p(lam), ctypes.c_void_p(out_host.data_ptr()), _p(ws), ws.numel(),
+                                   _stream(stream)))
+    return out_host
 
 
 def tk_assemble_objective(m: int, n: int, G: torch.Tensor, S: torch.Tensor, A: torch.Tensor,

@@ -355,4 +355,30 @@ int tk_objective(int m, int64_t n, int storage, const void *K, int64_t B, const 
   return TK_OK;
 }
 
+size_t tk_objective_host_workspace_size(int m, int64_t n) {
+  const size_t cws = tk_contract_workspace_size(m, n, 1);
+  if (cws == 0) return 0;
+  return ((cws + 255) & ~size_t(255)) + 2 * (((size_t)(n + 2) * sizeof(double) + 255) & ~size_t(255));
+}
+
+int tk_objective_host(int m, int64_t n, int storage, const void *K, const double *A_host, const double *y,
+                      const double *lambda, double *out_host, void *work, size_t work_bytes, void *stream) {
+  if (!A_host || !out_host) return fail(TK_EINVAL, "NULL host buffer");
+  const size_t need = tk_objective_host_workspace_size(m, n);
+  if (need == 0) return TK_EINVAL;
+  if (!work || work_bytes < need) return fail(TK_ENOMEM, "workspace %zu < %zu bytes", work_bytes, need);
+  const size_t cws = (tk_contract_workspace_size(m, n, 1) + 255) & ~size_t(255);
+  const size_t vec = ((size_t)(n + 2) * sizeof(double) + 255) & ~size_t(255);
+  unsigned char *wsb = reinterpret_cast<unsigned char *>(work);
+  double *a_dev = reinterpret_cast<double *>(wsb + cws);
+  double *out_dev = reinterpret_cast<double *>(wsb + cws + vec);  // F, |grad|, grad[0..n-1]
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  TK_CUDA_CHECK(cudaMemcpyAsync(a_dev, A_host, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st));
+  int rc = tk_objective(m, n, storage, K, 1, a_dev, y, lambda, out_dev, out_dev + 2, out_dev + 1, work, cws, stream);
+  if (rc != TK_OK) return rc;
+  TK_CUDA_CHECK(cudaMemcpyAsync(out_host, out_dev, (size_t)(n + 2) * sizeof(double), cudaMemcpyDeviceToHost, st));
+  TK_CUDA_CHECK(cudaStreamSynchronize(st));
+  return TK_OK;
+}
+
 }  // extern "C"

@@ -129,3 +129,21 @@ def test_rejects_bad_arguments():
         tk.tk_contract(K, 10, n, A)  # order above the supported maximum
     with pytest.raises(tk.TKError):
         tk.tk_contract(K[1:], m, n, A)  # K not 16-byte aligned
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_objective_with_host_buffers(storage):
+    # one C-ABI call: host alpha in, host [F, |grad|, grad] out; the same pass as tk_objective
+    m, n, d = 4, 33, 3
+    X, Kr, Kd = _setup(m, n, d, storage, salt=21)
+    a = synth.alpha_like(n, salt=22)
+    y = torch.tensor(synth.alpha_like(n, salt=23), device="cuda")
+    lam = torch.tensor([0.7], dtype=torch.float64, device="cuda")
+    out = tk.tk_objective_host(Kd, m, n, torch.tensor(a).pin_memory(), y, lam)
+    F, grad, gn = tk.tk_objective(Kd, m, n, torch.tensor(a, device="cuda"), y, lam)
+    assert out[0].item() == F.item() and out[1].item() == gn.item()
+    assert torch.equal(out[2:], grad.reshape(n).cpu())
+    g_ref, S_ref = oracle.contract(Kr, a, m)
+    F_ref = oracle.dual_objective(S_ref, a, y.cpu().numpy(), 0.7, m)
+    g_abs, S_abs = oracle.contract(np.abs(Kr), np.abs(a), m)
+    assert abs(out[0].item() - F_ref) <= float(contraction_bound(n, np.array([S_abs]), storage, m)[0]) / m + 1e-12 * abs(F_ref)
