@@ -3,6 +3,12 @@
     python -m paper_2003_10482_gb300.profile_case contract --m 4 --n 350 --storage f32 --reps 5
     python -m paper_2003_10482_gb300.profile_case batched --m 4 --n 300 --B 512 --reps 3
     python -m paper_2003_10482_gb300.profile_case build --m 4 --n 300 --d 80 --reps 2
+    python -m paper_2003_10482_gb300.profile_case dexter
+
+The `dexter` case is the Dexter-shaped run (n = 200 points, d = 20,000
+features at 0.5 % density, m = 4, FP32 storage): it times the packed build and
+a full Newton-CG dual solve (build once, solve to |grad F| <= 1e-6) and
+checks the solution against the closed-form gradient X (X^T a)^{o3} + lambda a - y.
 
 Inputs are the seeded synthetic ones of the benchmarks (X ~ U(-1, 1) rows of
 the full FP32 workload, or N(0, 1) rows of the batched workload's points);
@@ -22,7 +28,7 @@ import synth
 
 def main() -> None:
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["contract", "hvp", "batched", "batched_hvp", "build"])
+    ap.add_argument("case", choices=["contract", "hvp", "batched", "batched_hvp", "build", "dexter"])
     ap.add_argument("--m", type=int, default=4)
     ap.add_argument("--n", type=int, default=300)
     ap.add_argument("--d", type=int, default=80)
@@ -31,6 +37,8 @@ def main() -> None:
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     torch.cuda.set_device(0)
+    if args.case == "dexter":
+        return dexter()
     if args.case in ("contract", "hvp"):
         X = synth.full_fp32()["X"][: args.n]
     else:
@@ -61,6 +69,35 @@ def main() -> None:
     ms = e0.elapsed_time(e1) / args.reps
     print(f"{args.case} m={m} n={n} B={B} {args.storage}: {ms:.3f} ms per launch "
           f"({K.numel():,} packed entries, status {tk.tk_status_read(ws)})")
+
+
+def dexter() -> None:
+    import time
+
+    import numpy as np
+    p = synth.dexter_like()
+    m, X, y, lam = p["m"], p["X"], p["y"], p["lam"]
+    n, d = X.shape
+    Xd = torch.tensor(X, device="cuda")
+    yd = torch.tensor(y, device="cuda")
+    tk.tk_build_packed(Xd[:8], m, storage="f32")  # warm-up (module load)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    K = tk.tk_build_packed(Xd, m, storage="f32")
+    e1.record()
+    torch.cuda.synchronize()
+    build_ms = e0.elapsed_time(e1)
+    t0 = time.perf_counter()
+    A, rep, rc = tk.tk_solve_dual(K, m, n, yd, [lam], tol=1e-6, max_iter=100)
+    torch.cuda.synchronize()
+    solve_s = time.perf_counter() - t0
+    a = A[0].cpu().numpy()
+    u = X.T @ a
+    g_exact = X @ u ** (m - 1) + lam * a - y
+    print(f"dexter-shaped m={m} n={n} d={d} (density {np.mean(X != 0):.4f}), {K.numel():,} packed FP32 entries: "
+          f"build {build_ms:.1f} ms ({2 * d * K.numel() / build_ms / 1e9:.1f} TFLOP/s at 2d flop per entry); "
+          f"solve {solve_s:.3f} s, {rep[0]['iters']} Newton iterations, {rep[0]['passes']} passes, "
+          f"|grad F| {rep[0]['gradnorm']:.2e} (closed form at the solution {np.linalg.norm(g_exact):.2e}), rc {rc}")
 
 
 if __name__ == "__main__":

@@ -129,6 +129,24 @@ def batched_path(index: int = 4, n_points: int = 20_000, d: int = 80,
                 masks=masks, storage="f32")
 
 
+def dexter_like(index: int = 5, n: int = 200, d: int = 20_000, density: float = 0.005, s: int = 20) -> dict:
+    """Shaped like the thesis's Dexter runs (few points, very many sparse
+    features): n = 200 rows of d = 20,000 features, each feature nonzero with
+    probability 0.5 % (values ~ N(0, 1)); w* has s = 20 thesis-rule entries
+    among the features that have a nonzero in some row; sigma = 0.05; m = 4;
+    lambda = 1 (the thesis does not state its Dexter lambda)."""
+    rng = rng_for(index)
+    X = np.where(rng.random((n, d)) < density, rng.standard_normal((n, d)), 0.0)
+    used = np.flatnonzero(np.any(X != 0.0, axis=0))
+    w = np.zeros(d)
+    pos = rng.choice(used, size=min(s, used.size), replace=False)
+    h = rng.standard_normal(pos.size)
+    u = rng.random(pos.size)
+    w[pos] = np.sign(h) * (1.0 - 0.3 * u)
+    y = X @ w + 0.05 * rng.standard_normal(n)
+    return dict(name="dexter_like_m4_n200_d20000", m=4, X=X, y=y, w_true=w, lam=1.0, storage="f32")
+
+
 def alpha_like(n: int, salt: int, scale: float = 1.0, batch: int | None = None) -> np.ndarray:
     """Seeded dual vector(s) ~ N(0, scale^2) for contraction tests."""
     rng = rng_for(99, salt)

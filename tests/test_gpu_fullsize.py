@@ -88,3 +88,21 @@ def test_hvp_closed_form(built):
     rel = 1.01 * (U[storage] + k * U32) if storage == "bf16" else 1.01 * k * U32
     err = np.abs(HV.cpu().numpy() - hv_ref)
     assert np.all(err <= rel * hv_abs), float(np.max(err / (rel * hv_abs)))
+
+
+def test_dexter_shaped_build_and_contraction():
+    # few points, very many sparse features: the build is d-heavy (2d flops per entry)
+    p = synth.dexter_like()
+    m, X = p["m"], p["X"]
+    n, d = X.shape
+    K = tk.tk_build_packed(torch.tensor(X, device="cuda"), m, storage="f32")
+    a = synth.alpha_like(n, salt=31)
+    G, S = tk.tk_contract(K, m, n, torch.tensor(a, device="cuda"))
+    u = X.T @ a
+    g_ref = X @ u ** (m - 1)
+    uabs = np.abs(X).T @ np.abs(a)
+    g_abs = np.abs(X) @ uabs ** (m - 1)
+    k = (d + m + 2) + accumulation_depth(n, max_warp_triangles(m, n, "f32"))
+    err = np.abs(G.cpu().numpy() - g_ref)
+    assert np.all(err <= 1.01 * k * U32 * g_abs + 1e-30), float(np.max(err / (1.01 * k * U32 * g_abs + 1e-30)))
+    assert abs(float(S[0]) - float(np.sum(u ** m))) <= 1.01 * k * U32 * float(np.sum(uabs ** m))
