@@ -1,6 +1,7 @@
-// Host side of the packed contraction: launch configuration of the streaming
-// kernel (tk_contract_impl.cuh) and the fixed-order FP64 reduction of the
-// per-block partial sums.
+// Host side of the packed contraction: the cost-balanced cut of the packed
+// range into row-aligned pieces (cached per workspace), the launch
+// configuration and the launch of the streaming kernel (tk_contract_impl.cuh,
+// whose last block sums the per-block partials in a fixed order).
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -13,63 +14,6 @@ namespace tk {
 int contract_launch_f64(const KParams &, bool, int, int, int, size_t, cudaStream_t);
 int contract_launch_f32(const KParams &, bool, int, int, int, size_t, cudaStream_t);
 int contract_launch_bf16(const KParams &, bool, int, int, int, size_t, cudaStream_t);
-
-// ------------------------------------------------------------------ finalize
-template <int BS>
-__device__ double block_sum(double x, double *sh) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sh[wid] = x;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < BS / 32; ++i) t += sh[i];
-    sh[32] = t;
-  }
-  __syncthreads();
-  return sh[32];
-}
-
-__global__ void __launch_bounds__(256) finalize_kernel(FinalizeArgs f) {
-  __shared__ double sh[33];
-  const int n = f.n, ld = n + 2;
-  const int vec = (f.mode == 1) ? 1 : 0;
-  const double lam = (f.mode == 2) ? f.lambda[0] : 0.0;
-  double ssq = 0.0, aa = 0.0, ya = 0.0;
-  for (int l = threadIdx.x; l < n; l += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < f.grid; ++b) s += f.part[(size_t)b * 2 * ld + vec * ld + l];
-    if (f.mode == 2) {
-      const double a = f.alpha[l], gr = s + lam * a - f.y[l];
-      if (f.grad) f.grad[l] = gr;
-      ssq += gr * gr;
-      aa += a * a;
-      ya += f.y[l] * a;
-    } else {
-      if (f.mode == 1) s /= (double)(f.m - 1);
-      if (f.out_dtype == TK_F64) reinterpret_cast<double *>(f.G)[l] = s;
-      else reinterpret_cast<float *>(f.G)[l] = (float)s;
-    }
-  }
-  double S = 0.0;
-  if (threadIdx.x == 0)
-    for (int b = 0; b < f.grid; ++b) S += f.part[(size_t)b * 2 * ld + n];
-  if (f.mode == 0) {
-    if (threadIdx.x == 0 && f.S) f.S[0] = S;
-    return;
-  }
-  if (f.mode == 1) return;
-  const double tssq = block_sum<256>(ssq, sh);
-  const double taa = block_sum<256>(aa, sh);
-  const double tya = block_sum<256>(ya, sh);
-  if (threadIdx.x == 0) {
-    if (f.S) f.S[0] = S;
-    if (f.F) f.F[0] = S / f.m + 0.5 * lam * taa - tya;
-    if (f.gnorm) f.gnorm[0] = sqrt(tssq);
-  }
-}
 
 // ------------------------------------------------------------------ host
 static int pick_nc(int n) {
@@ -398,10 +342,5 @@ int contract_pass_static(const ContractArgs &a, WarpPlan *host_plan, int host_ca
   return contract_launch_bf16(kp, dual, r.nc, r.grid, r.warps * 32, r.smem, st);
 }
 
-int contract_finalize(const FinalizeArgs &f, cudaStream_t st) {
-  finalize_kernel<<<1, 256, 0, st>>>(f);
-  TK_CUDA_CHECK(cudaGetLastError());
-  return TK_OK;
-}
 
 }  // namespace tk

@@ -155,23 +155,6 @@ __device__ __forceinline__ Nm<T, D> warp_sum(Nm<T, D> a) {
 }
 
 template <typename ST, typename CT>
-__device__ __forceinline__ CT ld_ring(const unsigned char *ring, uint32_t idx);
-template <>
-__device__ __forceinline__ float ld_ring<float, float>(const unsigned char *ring, uint32_t idx) {
-  return reinterpret_cast<const float *>(ring)[idx];
-}
-template <>
-__device__ __forceinline__ double ld_ring<double, double>(const unsigned char *ring, uint32_t idx) {
-  return reinterpret_cast<const double *>(ring)[idx];
-}
-template <>
-__device__ __forceinline__ float ld_ring<__nv_bfloat16, float>(const unsigned char *ring,
-                                                                uint32_t idx) {
-  uint32_t h = reinterpret_cast<const unsigned short *>(ring)[idx];
-  return __uint_as_float(h << 16);
-}
-
-template <typename ST, typename CT>
 __device__ __forceinline__ CT ld_elem(const ST *p);
 template <>
 __device__ __forceinline__ float ld_elem<float, float>(const float *p) {

@@ -135,8 +135,6 @@ struct StaticPlanState {
 int contract_pass_static(const ContractArgs &a, WarpPlan *host_plan, int host_cap, StaticPlanState *state,
                          size_t scratch_bytes, int *grid_out, const double **part_out, cudaStream_t st);
 
-int contract_finalize(const FinalizeArgs &f, cudaStream_t st);
-
 // Bytes of the workspace regions (plan records for every warp of the largest
 // launch, then the per-block partial sums).
 size_t contract_plan_bytes(int sms);
