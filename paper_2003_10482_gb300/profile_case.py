@@ -4,11 +4,16 @@
     python -m paper_2003_10482_gb300.profile_case batched --m 4 --n 300 --B 512 --reps 3
     python -m paper_2003_10482_gb300.profile_case build --m 4 --n 300 --d 80 --reps 2
     python -m paper_2003_10482_gb300.profile_case dexter
+    python -m paper_2003_10482_gb300.profile_case nystrom
 
 The `dexter` case is the Dexter-shaped run (n = 200 points, d = 20,000
 features at 0.5 % density, m = 4, FP32 storage): it times the packed build and
 a full Newton-CG dual solve (build once, solve to |grad F| <= 1e-6) and
 checks the solution against the closed-form gradient X (X^T a)^{o3} + lambda a - y.
+The `nystrom` case runs the Nystrom configuration end to end for BF16, FP32
+and FP64 storage: 600 landmarks of 50,000 points (d = 200), build, Newton-CG
+solve, primal w = J_q(X^T a), prediction of 10,000 held-out points; it prints
+test MSE, the recovered support (|w_j| > 2 std(w)) against w*'s, and timings.
 
 Inputs are the seeded synthetic ones of the benchmarks (X ~ U(-1, 1) rows of
 the full FP32 workload, or N(0, 1) rows of the batched workload's points);
@@ -28,7 +33,7 @@ import synth
 
 def main() -> None:
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["contract", "hvp", "batched", "batched_hvp", "build", "dexter"])
+    ap.add_argument("case", choices=["contract", "hvp", "batched", "batched_hvp", "build", "dexter", "nystrom"])
     ap.add_argument("--m", type=int, default=4)
     ap.add_argument("--n", type=int, default=300)
     ap.add_argument("--d", type=int, default=80)
@@ -39,6 +44,8 @@ def main() -> None:
     torch.cuda.set_device(0)
     if args.case == "dexter":
         return dexter()
+    if args.case == "nystrom":
+        return nystrom()
     if args.case in ("contract", "hvp"):
         X = synth.full_fp32()["X"][: args.n]
     else:
@@ -98,6 +105,42 @@ def dexter() -> None:
           f"build {build_ms:.1f} ms ({2 * d * K.numel() / build_ms / 1e9:.1f} TFLOP/s at 2d flop per entry); "
           f"solve {solve_s:.3f} s, {rep[0]['iters']} Newton iterations, {rep[0]['passes']} passes, "
           f"|grad F| {rep[0]['gradnorm']:.2e} (closed form at the solution {np.linalg.norm(g_exact):.2e}), rc {rc}")
+
+
+def nystrom() -> None:
+    import time
+
+    import numpy as np
+    c = synth.nystrom_bf16()
+    m, lam = c["m"], c["lam"]
+    N = c["X_train"].shape[0]
+    idx = tk.tk_nystrom_select(N, c["n_prime"], c["select_seed"])
+    XL = torch.tensor(c["X_train"][idx], device="cuda")
+    yL = torch.tensor(c["y_train"][idx], device="cuda")
+    Xt = torch.tensor(c["X_test"], device="cuda")
+    n = XL.shape[0]
+    true_support = set(np.flatnonzero(c["w_true"]).tolist())
+    for storage in ("bf16", "f32", "f64"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        K = tk.tk_build_packed(XL, m, storage=storage)
+        torch.cuda.synchronize()
+        t_build = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        A, rep, rc = tk.tk_solve_dual(K, m, n, yL, [lam], tol=1e-8, max_iter=100)
+        torch.cuda.synchronize()
+        t_solve = time.perf_counter() - t0
+        W = tk.tk_primal(XL, A[0], m)
+        yhat = tk.tk_predict(Xt, W).cpu().numpy().reshape(-1)
+        mse = float(np.mean((yhat - c["y_test"]) ** 2))
+        sup = set(int(j) for j in tk.support_threshold(W))
+        hit = len(sup & true_support)
+        print(f"nystrom {storage}: {K.numel():,} entries ({K.numel() * K.element_size() / 1e9:.1f} GB); build "
+              f"{t_build:.2f} s; solve {t_solve:.2f} s ({rep[0]['iters']} iterations, {rep[0]['passes']} passes, "
+              f"|grad F| {rep[0]['gradnorm']:.1e}, rc {rc}); test MSE {mse:.6f}; support {len(sup)} found, "
+              f"{hit} of {len(true_support)} true", flush=True)
+        del K
+        torch.cuda.empty_cache()
 
 
 if __name__ == "__main__":
