@@ -10,10 +10,12 @@ The `dexter` case is the Dexter-shaped run (n = 200 points, d = 20,000
 features at 0.5 % density, m = 4, FP32 storage): it times the packed build and
 a full Newton-CG dual solve (build once, solve to |grad F| <= 1e-6) and
 checks the solution against the closed-form gradient X (X^T a)^{o3} + lambda a - y.
-The `nystrom` case runs the Nystrom configuration end to end for BF16, FP32
-and FP64 storage: 600 landmarks of 50,000 points (d = 200), build, Newton-CG
-solve, primal w = J_q(X^T a), prediction of 10,000 held-out points; it prints
-test MSE, the recovered support (|w_j| > 2 std(w)) against w*'s, and timings.
+The `nystrom` case runs the Nystrom configuration end to end for FP64, FP32
+and BF16 storage: 600 landmarks of 50,000 points (d = 200), build, Newton-CG
+solve to a 1e-7 relative gap (at most 40 iterations), primal
+w = J_q(X^T a), prediction of 10,000 held-out points; it prints each
+solution's objective under the FP64 tensor, test MSE, the recovered support
+(|w_j| > 2 std(w)) against w*'s, and timings.
 
 Inputs are the seeded synthetic ones of the benchmarks (X ~ U(-1, 1) rows of
 the full FP32 workload, or N(0, 1) rows of the batched workload's points);
@@ -120,16 +122,23 @@ def nystrom() -> None:
     Xt = torch.tensor(c["X_test"], device="cuda")
     n = XL.shape[0]
     true_support = set(np.flatnonzero(c["w_true"]).tolist())
-    for storage in ("bf16", "f32", "f64"):
+    lam_t = torch.tensor([lam], dtype=torch.float64, device="cuda")
+    K64 = None
+    F_ref = None
+    for storage in ("f64", "f32", "bf16"):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         K = tk.tk_build_packed(XL, m, storage=storage)
         torch.cuda.synchronize()
         t_build = time.perf_counter() - t0
         t0 = time.perf_counter()
-        A, rep, rc = tk.tk_solve_dual(K, m, n, yL, [lam], tol=1e-8, max_iter=100)
+        A, rep, rc = tk.tk_solve_dual(K, m, n, yL, [lam], tol=0.0, rel_gap=1e-7, max_iter=40)
         torch.cuda.synchronize()
         t_solve = time.perf_counter() - t0
+        if storage == "f64":
+            K64 = K
+            F_ref = rep[0]["F"]
+        F64, _, _ = tk.tk_objective(K64, m, n, A[0].contiguous(), yL, lam_t)
         W = tk.tk_primal(XL, A[0], m)
         yhat = tk.tk_predict(Xt, W).cpu().numpy().reshape(-1)
         mse = float(np.mean((yhat - c["y_test"]) ** 2))
@@ -137,10 +146,12 @@ def nystrom() -> None:
         hit = len(sup & true_support)
         print(f"nystrom {storage}: {K.numel():,} entries ({K.numel() * K.element_size() / 1e9:.1f} GB); build "
               f"{t_build:.2f} s; solve {t_solve:.2f} s ({rep[0]['iters']} iterations, {rep[0]['passes']} passes, "
-              f"|grad F| {rep[0]['gradnorm']:.1e}, rc {rc}); test MSE {mse:.6f}; support {len(sup)} found, "
-              f"{hit} of {len(true_support)} true", flush=True)
-        del K
-        torch.cuda.empty_cache()
+              f"|grad F| {rep[0]['gradnorm']:.1e}, rc {rc}); F under the FP64 tensor {float(F64[0]):.9f} "
+              f"(rel. to the FP64 solve {(float(F64[0]) - F_ref) / abs(F_ref):+.1e}); test MSE {mse:.6f}; "
+              f"support {len(sup)} found, {hit} of {len(true_support)} true", flush=True)
+        if storage != "f64":
+            del K
+    torch.cuda.empty_cache()
 
 
 if __name__ == "__main__":
