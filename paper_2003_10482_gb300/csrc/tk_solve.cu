@@ -315,6 +315,10 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
   std::vector<double> one(B, 1.0), zero(B, 0.0), minus1(B, -1.0), ca(B), cb(B), flag(B);
   std::vector<int> status(B, TK_ENOTCONV), iters(B, 0), passes(B, 0);
   std::vector<char> active(B, 1), stalled(B, 0);
+  // non-positive curvature met in the inner solve: with the exact tensor the
+  // Hessian (m-1) K[a^{m-2}] + lambda I is positive definite, so only a rounded
+  // (FP32/BF16) stored tensor can show it -- its form is indefinite at the iterate
+  std::vector<char> indefinite(B, 0);
 
   if (P->mask) {
     k_mask<<<grid_for(B * n), 256, 0, s.st>>>(B, n, P->mask, A);
@@ -358,7 +362,10 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
         TK_TRY(s.dots(s.w.d, s.w.Hd, dHd));
         for (int64_t b = 0; b < B; ++b) {
           ca[b] = (cg[b] && dHd[b] > 0) ? rr[b] / dHd[b] : 0.0;
-          if (cg[b] && !(dHd[b] > 0)) cg[b] = 0;  // (H is positive definite; guards rounding)
+          if (cg[b] && !(dHd[b] > 0)) {  // (H is positive definite; guards rounding)
+            cg[b] = 0;
+            indefinite[b] = 1;
+          }
         }
         std::vector<double> nca(B);
         for (int64_t b = 0; b < B; ++b) nca[b] = -ca[b];
@@ -480,6 +487,10 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
   }
   TK_CUDA_CHECK(cudaStreamSynchronize(s.st));
   for (int64_t b = 0; b < B; ++b)
-    if (R[b].status != TK_OK) return fail(TK_ENOTCONV, "problem %lld stopped at |grad F| = %.3e", (long long)b, R[b].gradnorm);
+    if (R[b].status != TK_OK)
+      return fail(TK_ENOTCONV, "problem %lld stopped at |grad F| = %.3e%s", (long long)b, R[b].gradnorm,
+                  indefinite[b] ? " after meeting non-positive curvature: the stored tensor's form is indefinite at "
+                                  "the iterate (its rounding breaks the sum of m-th powers; see the storage dtype)"
+                                : "");
   return TK_OK;
 }
