@@ -171,7 +171,8 @@ def cpu_baseline_leg(target_s: float = 2.5) -> dict:
     dt = _time_oracle(K, a, m)
     eps = K.shape[0] / dt
     return {"value": eps * 4 / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": _sample_text(K.shape[0]), "entries_per_s": eps, "seconds": dt}
+            "sample": _sample_text(K.shape[0]), "entries_per_s": eps, "seconds": dt,
+            "host_cores": os.cpu_count(), "affinity_cores": len(os.sched_getaffinity(0))}
 
 
 def run_reference(args) -> None:
