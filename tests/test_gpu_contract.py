@@ -147,3 +147,38 @@ def test_objective_with_host_buffers(storage):
     F_ref = oracle.dual_objective(S_ref, a, y.cpu().numpy(), 0.7, m)
     g_abs, S_abs = oracle.contract(np.abs(Kr), np.abs(a), m)
     assert abs(out[0].item() - F_ref) <= float(contraction_bound(n, np.array([S_abs]), storage, m)[0]) / m + 1e-12 * abs(F_ref)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_largest_point_count(storage):
+    # n = TK_MAX_POINTS: 32 column chunks per lane, the widest register configuration
+    m, n, d = 2, 1024, 3
+    X, Kr, Kd = _setup(m, n, d, storage, salt=41)
+    a = synth.alpha_like(n, salt=42)
+    v = synth.alpha_like(n, salt=43)
+    G, S = tk.tk_contract(Kd, m, n, torch.tensor(a, device="cuda"))
+    g_ref, S_ref = oracle.contract(Kr, a, m)
+    g_abs, S_abs = oracle.contract(np.abs(Kr), np.abs(a), m)
+    assert np.all(np.abs(G.cpu().numpy() - g_ref) <= contraction_bound(n, g_abs, storage, m))
+    assert abs(float(S[0]) - S_ref) <= float(contraction_bound(n, np.array([S_abs]), storage, m)[0])
+    HV, _ = tk.tk_contract(Kd, m, n, torch.tensor(a, device="cuda"), r=m - 2, V=torch.tensor(v, device="cuda"))
+    hv_ref = oracle.hvp(Kr, a, v, m)
+    hv_abs = oracle.hvp(np.abs(Kr), np.abs(a), np.abs(v), m)
+    assert np.all(np.abs(HV.cpu().numpy() - hv_ref) <= 2 * contraction_bound(n, hv_abs, storage, m, dual=True))
+
+
+def test_point_count_above_the_limit_is_refused():
+    m, n = 2, 1025
+    K = torch.zeros(tk.tk_packed_size(m, n), dtype=torch.float32, device="cuda")
+    A = torch.zeros(n, dtype=torch.float64, device="cuda")
+    with pytest.raises(tk.TKError):
+        tk.tk_contract(K, m, n, A)
+
+
+def test_empty_shard_contributes_nothing():
+    m, n, d = 4, 20, 3
+    X, Kr, Kd = _setup(m, n, d, "f32", salt=44)
+    lo = tk.tk_row_align(m, n, tk.tk_packed_size(m, n) // 2)
+    A = torch.tensor(synth.alpha_like(n, salt=45), device="cuda")
+    G, S = tk.tk_contract(Kd[lo:lo + 1].clone(), m, n, A, off_lo=lo, off_hi=lo)
+    assert torch.count_nonzero(G).item() == 0 and float(S[0]) == 0.0
