@@ -249,6 +249,14 @@ int tk_contract_noalloc(int m, int64_t n, int storage_dtype, const void *K, int 
  * `stream`. */
 int tk_status_read(void *work, void *stream);
 
+/* Diagnostic: one block waits, with the library's bounded wait and a budget of
+ * `budget_cycles` SM cycles (1 .. 2^31), on an mbarrier that nothing arrives
+ * on, then records TK_ETIMEOUT in the status word of `work` (at least its
+ * 256-byte header) as every kernel does when a wait runs out; tk_status_read
+ * returns it.  The wait ends by itself and the context stays usable: the
+ * timeout path can be tested without faulting or hanging the device. */
+int tk_check_bounded_wait(void *work, size_t work_bytes, long long budget_cycles, void *stream);
+
 /* ------------------------------------------------------------ dual objective */
 
 /* Dual objective and gradient (Section 4, eqs. dual_tensor_kernel and jq, with

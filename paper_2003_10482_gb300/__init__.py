@@ -72,6 +72,7 @@ def _declare(L):
         "tk_contract": (i32, [i32, i64, i32, P, i64, i32, P, i32, P, P, P, P, sz, P]),
         "tk_contract_range": (i32, [i32, i64, i32, P, i64, i64, i64, i32, P, i32, P, P, P, P, sz, P]),
         "tk_status_read": (i32, [P, P]),
+        "tk_check_bounded_wait": (i32, [P, sz, ctypes.c_longlong, P]),
         "tk_contract_set_config": (i32, [P]),
         "tk_contract_get_config": (i32, [i32, i64, i32, i32, P]),
         "tk_batched_set_config": (i32, [P]),
@@ -232,6 +233,12 @@ def tk_batched_get_config(m: int, n: int, storage="f32", dual: bool = False, B: 
     c = tk_batched_config()
     _check(lib().tk_batched_get_config(m, n, dtype_code(storage), int(dual), B, ctypes.byref(c)))
     return {f: getattr(c, f) for f, _ in c._fields_}
+
+
+def tk_check_bounded_wait(work: torch.Tensor, budget_cycles: int = 1 << 22, stream=None) -> None:
+    """Run the library's bounded device wait on a barrier nothing arrives on
+    (diagnostic); the status word of `work` then reads TK_ETIMEOUT."""
+    _check(lib().tk_check_bounded_wait(_p(work), work.numel(), budget_cycles, _stream(stream)))
 
 
 def tk_status_read(work: torch.Tensor, stream=None) -> int:

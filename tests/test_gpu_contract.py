@@ -182,3 +182,18 @@ def test_empty_shard_contributes_nothing():
     A = torch.tensor(synth.alpha_like(n, salt=45), device="cuda")
     G, S = tk.tk_contract(Kd[lo:lo + 1].clone(), m, n, A, off_lo=lo, off_hi=lo)
     assert torch.count_nonzero(G).item() == 0 and float(S[0]) == 0.0
+
+
+def test_bounded_wait_times_out_and_the_context_stays_usable():
+    # a device wait that runs out reports TK_ETIMEOUT through the status word;
+    # the wait ends by itself (no fault, no hang) and the next call works
+    ws = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    tk.tk_check_bounded_wait(ws, budget_cycles=1 << 20)
+    assert tk.tk_status_read(ws) == tk.TK_ETIMEOUT
+    assert tk.tk_status_read(ws) == tk.TK_OK  # reading clears it
+    m, n, d = 4, 12, 3
+    X, Kr, Kd = _setup(m, n, d, "f64", salt=46)
+    a = synth.alpha_like(n, salt=47)
+    G, S = tk.tk_contract(Kd, m, n, torch.tensor(a, device="cuda"))
+    g_ref, _ = oracle.contract(Kr, a, m)
+    assert np.allclose(G.cpu().numpy(), g_ref, rtol=1e-10, atol=1e-12)
