@@ -52,6 +52,7 @@ def tune_contract(K: torch.Tensor, m: int, n: int, dual: bool = False, reps: int
     if candidates is None:
         candidates = [dict(warps=w, block_bytes=bb, nbuf=nb, schedule=sc)
                       for w, bb, nb, sc in itertools.product((14, 16), (0, 4224), (2, 3), (1, 2))]
+        candidates += [dict(pieces_per_warp=pp) for pp in (8, 12)] + [dict(row_cost=256, tri_cost=4096)]
     A = _vectors(n, 1, 1)[0]
     V = _vectors(n, 1, 2)[0]
     ws = tk.workspace(m, n)

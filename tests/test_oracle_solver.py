@@ -128,3 +128,15 @@ def test_nystrom_subsets_are_uniform():
     chi2 = sum((c - exp) ** 2 / exp for c in counts.values())
     # 34 degrees of freedom: P(chi2 > 70) < 1e-3
     assert chi2 < 70
+
+
+def test_dexter_shaped_generator():
+    # 0.5 % density, w* supported on features that occur in some row, thesis-rule values
+    p = synth.dexter_like()
+    X, w = p["X"], p["w_true"]
+    assert X.shape == (200, 20_000)
+    assert abs(np.mean(X != 0.0) - 0.005) < 0.0005
+    sup = np.flatnonzero(w)
+    assert sup.size == 20 and np.all(np.any(X[:, sup] != 0.0, axis=0))
+    assert np.all((np.abs(w[sup]) >= 0.7) & (np.abs(w[sup]) <= 1.0))
+    assert np.allclose(p["y"], X @ w, atol=0.05 * 6)
