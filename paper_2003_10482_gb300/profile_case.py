@@ -20,8 +20,8 @@ solution's objective under the FP64 tensor, test MSE, the recovered support
 Inputs are the seeded synthetic ones of the benchmarks (X ~ U(-1, 1) rows of
 the full FP32 workload, or N(0, 1) rows of the batched workload's points);
 each case builds its packed tensor once, then launches the kernel `--reps`
-times (the first launches are warm-up for `ncu -s`).  Prints the mean
-CUDA-event time per launch.
+more times after one warm-up launch (skip it with `ncu -s 1`).  Prints the
+mean CUDA-event time per timed launch.
 """
 from __future__ import annotations
 
@@ -68,6 +68,7 @@ def main() -> None:
     else:
         def run():
             tk.tk_contract(K, m, n, A, r=m - 2, V=V, work=ws)
+    run()  # warm-up: module load, work plan (the profiler's -s 1 skips this launch)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
