@@ -134,12 +134,13 @@ size_t tk_contract_workspace_size(int m, int64_t n, int64_t B);
  * A, V, G: B x n row-major, vec_dtype TK_F64 or TK_F32.  S: B FP64 values.
  * Arithmetic: FP64 for TK_F64 storage; FP32 for TK_F32 / TK_BF16 storage with
  * the cross-block reduction and S in FP64.  Each packed entry is read from
- * HBM once per pass.  For TK_F32 / TK_BF16 storage and B >= 28 (B >= 16 for
- * r = m-2) one launch serves the whole batch (each entry read once for all B
- * vectors, 2B multiply-adds per entry; 4B for r = m-2); otherwise the
- * single-vector pass runs once per b.  Asynchronous; errors that only the device can see
- * (a bounded wait that ran out) are recorded in `work` and returned by
- * tk_status_read. */
+ * HBM once per pass.  For TK_F32 / TK_BF16 storage and B at least the
+ * batched configuration's min_batch (by default 28, or 16 for r = m-2; see
+ * tk_batched_config) one launch serves the whole batch (each entry read once
+ * for all B vectors, 2B multiply-adds per entry; 4B for r = m-2); otherwise
+ * the single-vector pass runs once per b.  Asynchronous; errors that only the
+ * device can see (a bounded wait that ran out) are recorded in `work` and
+ * returned by tk_status_read. */
 int tk_contract(int m, int64_t n, int storage_dtype, const void *K, int64_t B,
                 int vec_dtype, const void *A, int r, const void *V, void *G,
                 double *S, void *work, size_t work_bytes, void *stream);
