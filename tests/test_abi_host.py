@@ -1,6 +1,5 @@
 """Host-side checks of libtk that need no GPU: the library loads, exports every
 symbol include/tk.h declares, and its layout helpers agree with the oracle."""
-import ctypes
 import subprocess
 
 import numpy as np
