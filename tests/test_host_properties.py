@@ -1,6 +1,7 @@
-"""Property-based checks of the library's host logic (no GPU): the ranking
+"""Property-based checks (no GPU): the library's host logic -- the ranking
 bijection, row alignment and the cost-balanced cut of a range, on random
-orders, point counts, offsets and piece counts."""
+orders, point counts, offsets and piece counts -- and the oracle's packed
+contraction and HVP against the dense n^m tensor on random tiny data."""
 import math
 
 import pytest
@@ -65,3 +66,25 @@ def test_plan_cuts_are_ordered_row_starts(m, n, pieces, a, b, rc, tc):
     assert all(x <= y for x, y in zip(cuts[:-1], cuts[1:]))
     for c in cuts:
         assert c == N or tk.tk_row_align(m, n, c) == c
+
+
+@settings(max_examples=60, deadline=None)
+@given(m=st.integers(2, 5), n=st.integers(1, 5), d=st.integers(1, 3), seed=st.integers(0, 2**31 - 1))
+def test_oracle_contraction_equals_the_full_tensor(m, n, d, seed):
+    # the packed contraction (multiplicity-weighted) against the dense n^m tensor, any data
+    import numpy as np
+
+    from brute import contract_full, full_tensor
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, d))
+    a = rng.standard_normal(n)
+    v = rng.standard_normal(n)
+    K = oracle.build(X, m)
+    g, S = oracle.contract(K, a, m)
+    T = full_tensor(X, m)
+    g_ref = contract_full(T, a, m - 1)
+    scale = max(1.0, float(np.abs(g_ref).max()))
+    assert np.allclose(g, g_ref, rtol=1e-11, atol=1e-11 * scale)
+    assert abs(S - float(g_ref @ a)) <= 1e-11 * max(1.0, abs(float(g_ref @ a)))
+    hv_ref = contract_full(T, a, m - 2) @ v
+    assert np.allclose(oracle.hvp(K, a, v, m), hv_ref, rtol=1e-11, atol=1e-11 * max(1.0, float(np.abs(hv_ref).max())))
