@@ -434,8 +434,23 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(_spawn_ranks(args.gpus))
     else:
         run_ours(args)
+
+
+def _spawn_ranks(nproc: int) -> int:
+    """`--gpus N` without a launcher: start N ranks on this node the way
+    torchrun would (one process per GPU, rendezvous on 127.0.0.1); rank 0
+    prints the JSON line."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={nproc}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
 
 
 if __name__ == "__main__":

@@ -117,8 +117,11 @@ int tk_build_packed_range(int m, int64_t n, int64_t d, const double *X, int feat
 
 /* Bytes of workspace tk_contract / tk_objective need for (m, n, B).  The
  * workspace carries a cached copy of the per-warp work plan between calls
- * (reused while m, n, the range and the launch configuration stay the same):
- * callers must not write into it. */
+ * (reused while m, n, the range and the launch configuration stay the same,
+ * keyed by the workspace's address): callers must not write into it, and call
+ * tk_workspace_release on memory that is new at an address a workspace held
+ * before.  Its header records the plan's key, which every contraction checks
+ * before it reads the plan (TK_EINVAL through tk_status_read on a mismatch). */
 size_t tk_contract_workspace_size(int m, int64_t n, int64_t B);
 
 /* Contractions of the symmetric tensor over its packed entries, each equal to
@@ -236,18 +239,38 @@ int tk_contract_plan(int m, int64_t n, int64_t off_lo, int64_t off_hi, int piece
  * (status header, work plan, per-block partials) must fit in it, else
  * TK_ENOMEM with the size it would need.  No cudaMalloc, cudaFree or other
  * allocator is called.  The first call on a device looks the array up
- * (cudaGetSymbolAddress), zeroes its header and uploads the work plan, and
- * later calls upload a plan only when (m, n) or the configuration changes:
- * make the first call for a given shape before any stream capture.  Every
- * call on a device shares the array and leaves the last call's contents in
- * it; calls whose executions overlap on the GPU (other streams, other host
- * threads' streams) race on it and must be serialised by the caller. */
+ * (cudaGetSymbolAddress) and zeroes its header; a call whose shape (m, n)
+ * or launch configuration (tk_contract_set_config) differs from the previous
+ * call's re-plans: it uploads the work plan from host memory and waits for
+ * the copy.  Make the first call, and the first call after every change of
+ * shape or configuration, outside stream capture: under capture such a call
+ * returns TK_EINVAL before it issues anything, so the capture stays valid.
+ * Every call on a device shares the array and leaves the last call's contents
+ * in it; calls whose executions overlap on the GPU (other streams, other host
+ * threads' streams) race on it and must be serialised by the caller.  A
+ * captured call replayed after a later call re-planned the array for another
+ * shape finds the plan key in the array's header changed, writes nothing to G
+ * or S and records TK_EINVAL, which tk_contract_noalloc_status returns. */
 int tk_contract_noalloc(int m, int64_t n, int storage_dtype, const void *K, int vec_dtype, const void *alpha,
                         void *G, double *S, void *stream);
 
-/* Reads (and clears) the device-side status word of a workspace: TK_OK, or
- * TK_ETIMEOUT if a bounded wait of an earlier call on it ran out.  Synchronises
- * `stream`. */
+/* Reads and clears the status word of the tk_contract_noalloc scratch on the
+ * current device: TK_OK, TK_ETIMEOUT (a bounded wait of an earlier call ran
+ * out) or TK_EINVAL (a replayed call found the scratch planned for another
+ * shape).  Synchronises `stream`.  TK_OK when no call ran on this device. */
+int tk_contract_noalloc_status(void *stream);
+
+/* Host only: forget which work plan the workspace at `work` holds.  A
+ * workspace caches its plan between calls, keyed by its address; call this
+ * before handing the library new memory at an address that held a workspace
+ * earlier (a freed and reallocated buffer), or after writing into a
+ * workspace, so that the next call uploads the plan again. */
+int tk_workspace_release(void *work);
+
+/* Reads (and clears) the device-side status word of a workspace: TK_OK,
+ * TK_ETIMEOUT if a bounded wait of an earlier call on it ran out, or TK_EINVAL
+ * if a contraction found the workspace's plan region planned for another
+ * shape (a replayed CUDA graph) and did nothing.  Synchronises `stream`. */
 int tk_status_read(void *work, void *stream);
 
 /* Diagnostic: one block waits, with the library's bounded wait and a budget of
@@ -295,6 +318,16 @@ int tk_assemble_objective(int m, int64_t n, int64_t B, const double *G, const do
                           const double *y, const double *lambda, double *F, double *grad, double *gnorm,
                           void *stream);
 
+/* Hessian-vector products of the dual objective (Section 4, second derivative
+ * of eq. dual_tensor_kernel, lambda = 1/gamma), FP64 on the device:
+ *   HV[b] = (m-1) K[A_b^{m-2}, V_b] + lambda_b V_b
+ * A, V, HV: B x n FP64; lambda: B FP64 (all device).  One dual-number pass
+ * over K (tk_contract with r = m-2) and an elementwise finish; the workspace
+ * is tk_contract's for (m, n, B). */
+int tk_dual_hvp(int m, int64_t n, int storage_dtype, const void *K, int64_t B, const double *A,
+                const double *V, const double *lambda, double *HV, void *work, size_t work_bytes,
+                void *stream);
+
 /* ------------------------------------------------------------ primal side */
 
 /* Representer map of Section 4 (eq. tensor_representer) for the linear tensor
@@ -307,6 +340,13 @@ int tk_primal(int m, int64_t n, int64_t d, const double *X, int64_t B, const dou
  * Yhat[b][j] = <w_b, x_j> for the t rows of Xtest (t x d row-major).
  * W: B x d, Yhat: B x t; FP64 device pointers. */
 int tk_predict(int64_t t, int64_t d, const double *Xtest, int64_t B, const double *W, double *Yhat, void *stream);
+
+/* Adaptive feature selection of Section 6.3: keep[b][j] = 1 when
+ * |W[b][j]| > 2 std(W[b]) (population standard deviation over the d weights
+ * of problem b), else 0; count[b] = number kept (count may be NULL).
+ * W: B x d FP64, keep: B x d bytes, count: B int64 (device).  FP64 sums in a
+ * fixed order, so the decision is reproducible. */
+int tk_support_threshold(int64_t d, int64_t B, const double *W, uint8_t *keep, int64_t *count, void *stream);
 
 /* Nystrom-like subsampling of Section 6.1: n_prime of the N training indices,
  * uniform without replacement, sorted ascending, written to idx_host (host).
@@ -333,6 +373,13 @@ typedef struct {
     int64_t B;              /* number of problems */
     const double *lambda;   /* B regularisation weights (device) */
     const uint8_t *mask;    /* B x n, 1 = point kept, 0 = held out (device); NULL = all kept */
+    const void *K_hvp;      /* optional second copy of the same tensor (N entries of
+                               hvp_storage_dtype, device) that the Hessian-vector passes of
+                               Newton-CG read instead of K; NULL = K.  The objective and
+                               gradient (which fix the minimiser) always read K, so a
+                               BF16 copy here halves the bytes of most passes while the
+                               solution stays that of K's precision */
+    int hvp_storage_dtype;
 } tk_problem;
 
 typedef struct {

@@ -83,6 +83,10 @@ def _declare(L):
         "tk_objective_host_workspace_size": (sz, [i32, i64]),
         "tk_objective_host": (i32, [i32, i64, i32, P, P, P, P, P, P, sz, P]),
         "tk_contract_noalloc": (i32, [i32, i64, i32, P, i32, P, P, P, P]),
+        "tk_contract_noalloc_status": (i32, [P]),
+        "tk_workspace_release": (i32, [P]),
+        "tk_dual_hvp": (i32, [i32, i64, i32, P, i64, P, P, P, P, P, sz, P]),
+        "tk_support_threshold": (i32, [i64, i64, P, P, P, P]),
         "tk_solve_workspace_size": (sz, [P]),
         "tk_primal": (i32, [i32, i64, i64, P, i64, P, P, P]),
         "tk_predict": (i32, [i64, i64, P, i64, P, P, P]),
@@ -179,8 +183,16 @@ def workspace(m: int, n: int, B: int = 1, device=None) -> torch.Tensor:
     key = dev.index
     t = _ws_cache.get(key)
     if t is None or t.numel() < need:
-        t = torch.zeros(need, dtype=torch.uint8, device=dev)
+        t = new_workspace(need, dev)
         _ws_cache[key] = t
+    return t
+
+
+def new_workspace(nbytes: int, device) -> torch.Tensor:
+    """Zeroed device memory for a workspace; the library forgets any work plan it
+    recorded for a workspace that used this address before."""
+    t = torch.zeros(nbytes, dtype=torch.uint8, device=device)
+    _check(lib().tk_workspace_release(_p(t)))
     return t
 
 
@@ -342,12 +354,29 @@ def tk_objective_host(K: torch.Tensor, m: int, n: int, A_host: torch.Tensor, y: 
         raise TKError(TK_EINVAL, lib().tk_last_error().decode())
     ws = _host_ws.get(dev.index)
     if ws is None or ws.numel() < need:
-        ws = torch.zeros(need, dtype=torch.uint8, device=dev)
+        ws = new_workspace(need, dev)
         _host_ws[dev.index] = ws
     _check(lib().tk_objective_host(m, n, dtype_code(K.dtype), _p(K), ctypes.c_void_p(A_host.data_ptr()),
                                    _p(y), _p(lam), ctypes.c_void_p(out_host.data_ptr()), _p(ws), ws.numel(),
                                    _stream(stream)))
     return out_host
+
+
+def tk_dual_hvp(K: torch.Tensor, m: int, n: int, A: torch.Tensor, V: torch.Tensor, lam,
+                work: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """(m-1) K[a^{m-2}, v] + lam v for each row of A and V (the dual Hessian times v), FP64."""
+    A2 = A.reshape(-1, n).to(torch.float64).contiguous()
+    B = A2.shape[0]
+    V2 = V.reshape(B, n).to(torch.float64).contiguous()
+    lam_t = torch.as_tensor(lam, dtype=torch.float64, device=A.device).reshape(-1)
+    if lam_t.numel() == 1 and B > 1:
+        lam_t = lam_t.expand(B).contiguous()
+    HV = torch.empty_like(A2)
+    if work is None:
+        work = workspace(m, n, B, A.device)
+    _check(lib().tk_dual_hvp(m, n, dtype_code(K.dtype), _p(K), B, _p(A2), _p(V2), _p(lam_t), _p(HV),
+                             _p(work), work.numel(), _stream(stream)))
+    return HV.reshape(A.shape)
 
 
 def tk_assemble_objective(m: int, n: int, G: torch.Tensor, S: torch.Tensor, A: torch.Tensor,
@@ -378,10 +407,17 @@ def tk_contract_noalloc(K: torch.Tensor, m: int, n: int, alpha: torch.Tensor, G:
     return G, S
 
 
+def tk_contract_noalloc_status(stream=None) -> int:
+    """Read and clear the status word of tk_contract_noalloc's static scratch on the
+    current device (synchronises the stream): TK_OK, TK_ETIMEOUT or TK_EINVAL."""
+    return int(lib().tk_contract_noalloc_status(_stream(stream)))
+
+
 class tk_problem(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int64), ("storage_dtype", ctypes.c_int),
                 ("K", ctypes.c_void_p), ("y", ctypes.c_void_p), ("B", ctypes.c_int64),
-                ("lam", ctypes.c_void_p), ("mask", ctypes.c_void_p)]
+                ("lam", ctypes.c_void_p), ("mask", ctypes.c_void_p), ("K_hvp", ctypes.c_void_p),
+                ("hvp_storage_dtype", ctypes.c_int)]
 
 
 class tk_solve_opts(ctypes.Structure):
@@ -399,11 +435,13 @@ _solve_ws: dict = {}
 
 def tk_solve_dual(K: torch.Tensor, m: int, n: int, y: torch.Tensor, lam, alpha0: torch.Tensor | None = None,
                   mask: torch.Tensor | None = None, method: str = "newton_cg", tol: float = 1e-10,
-                  max_iter: int = 100, max_cg: int = 0, rel_gap: float = 0.0, stream=None):
+                  max_iter: int = 100, max_cg: int = 0, rel_gap: float = 0.0, K_hvp: torch.Tensor | None = None,
+                  stream=None):
     """Solve B dual problems over the packed tensor K.  Returns (alpha (B x n FP64),
     reports (list of dicts), rc) where rc is TK_OK or TK_ENOTCONV.  A problem
     stops when |grad F| <= tol or (Newton-CG, rel_gap > 0) when its Newton
-    decrement estimate of F - F* is <= rel_gap * max(1, |F|)."""
+    decrement estimate of F - F* is <= rel_gap * max(1, |F|).  K_hvp: an optional
+    lower-precision copy of K that only the Hessian-vector passes read."""
     dev = K.device
     lam_t = torch.as_tensor(lam, dtype=torch.float64, device=dev).reshape(-1).contiguous()
     B = lam_t.numel()
@@ -412,7 +450,8 @@ def tk_solve_dual(K: torch.Tensor, m: int, n: int, y: torch.Tensor, lam, alpha0:
     yd = y.to(dev, torch.float64).contiguous()
     mk = None if mask is None else mask.reshape(B, n).to(dev, torch.uint8).contiguous()
     prob = tk_problem(m, n, dtype_code(K.dtype), K.data_ptr(), yd.data_ptr(), B, lam_t.data_ptr(),
-                      0 if mk is None else mk.data_ptr())
+                      0 if mk is None else mk.data_ptr(), 0 if K_hvp is None else K_hvp.data_ptr(),
+                      0 if K_hvp is None else dtype_code(K_hvp.dtype))
     opts = tk_solve_opts(TK_NEWTON_CG if method == "newton_cg" else TK_GD_BT, tol, max_iter, max_cg, 0.0, rel_gap)
     need = int(lib().tk_solve_workspace_size(ctypes.byref(prob)))
     if need == 0:
@@ -420,7 +459,7 @@ def tk_solve_dual(K: torch.Tensor, m: int, n: int, y: torch.Tensor, lam, alpha0:
     key = dev.index
     ws = _solve_ws.get(key)
     if ws is None or ws.numel() < need:
-        ws = torch.zeros(need, dtype=torch.uint8, device=dev)
+        ws = new_workspace(need, dev)
         _solve_ws[key] = ws
     reps = (tk_solve_report * B)()
     rc = lib().tk_solve_dual(ctypes.byref(prob), ctypes.byref(opts), _p(A), reps, _p(ws), ws.numel(),
@@ -458,8 +497,19 @@ def tk_nystrom_select(N: int, n_prime: int, seed: int) -> list[int]:
     return list(out)[:n_prime]
 
 
-def support_threshold(w) -> list[int]:
-    """Features with |w_j| > 2 std(w) (the adaptive threshold of Section 6.3); host."""
-    import numpy as np
-    w = np.asarray(w.detach().cpu() if hasattr(w, "detach") else w, dtype=np.float64)
-    return list(np.nonzero(np.abs(w) > 2.0 * np.std(w))[0])
+def tk_support_threshold(W: torch.Tensor, stream=None):
+    """keep[b][j] = |W[b][j]| > 2 std(W[b]) (Section 6.3) for a (d,) or (B, d) FP64
+    device tensor; returns (keep (uint8, shaped like W), count (B,) int64)."""
+    W2 = W.reshape(-1, W.shape[-1]).to(torch.float64).contiguous()
+    B, d = W2.shape
+    keep = torch.empty(B, d, dtype=torch.uint8, device=W.device)
+    cnt = torch.empty(B, dtype=torch.int64, device=W.device)
+    _check(lib().tk_support_threshold(d, B, _p(W2), _p(keep), _p(cnt), _stream(stream)))
+    return keep.reshape(W.shape), cnt
+
+
+def support_threshold(w: torch.Tensor) -> list[int]:
+    """Indices of the features kept by the 2 std threshold of Section 6.3 (one
+    weight vector, computed on the device by tk_support_threshold)."""
+    keep, _ = tk_support_threshold(w.reshape(-1))
+    return torch.nonzero(keep).reshape(-1).tolist()

@@ -302,10 +302,21 @@ int tk_status_read(void *work, void *stream) {
   TK_CUDA_CHECK(cudaStreamSynchronize(st));
   if (h.status != TK_OK) {
     int code = h.status;
-    TK_CUDA_CHECK(cudaMemsetAsync(work, 0, sizeof(WsHeader), st));
+    // clear the status word and its site only: the rest of the header records
+    // which work plan the workspace holds
+    TK_CUDA_CHECK(cudaMemsetAsync(work, 0, 2 * sizeof(int), st));
     TK_CUDA_CHECK(cudaStreamSynchronize(st));
+    if (h.where == kSiteStalePlan)
+      return fail(code, "a contraction found its workspace planned for another shape and did nothing "
+                  "(a CUDA graph replayed after a later call with another shape re-planned it)");
     return fail(code, "device status %d (site %d)", code, h.where);
   }
+  return TK_OK;
+}
+
+int tk_workspace_release(void *work) {
+  if (!work) return fail(TK_EINVAL, "NULL workspace");
+  forget_plan(work);
   return TK_OK;
 }
 

@@ -130,6 +130,7 @@ __global__ void __launch_bounds__(kBT, 1) batched_kernel(BParams p) {
   const int m = p.m, n = p.n;
   const int g = blockIdx.x / p.slices;
   const int sidx = blockIdx.x % p.slices;
+  if (plan_is_stale(p.status, m, n, p.pieces, p.off_lo, p.off_hi)) return;
 
   float *a_s = reinterpret_cast<float *>(smem);  // [n][BL] (value), then [n][BL] (direction)
   float *v_s = a_s + (size_t)n * BL;
@@ -389,7 +390,7 @@ __global__ void __launch_bounds__(kBT, 1) batched_kernel(BParams p) {
       if (!mbar_wait_bounded(&bar[bi], parity)) {
         if (lane == 0) {
           atomicExch(&reinterpret_cast<WsHeader *>(p.status)->status, TK_ETIMEOUT);
-          reinterpret_cast<WsHeader *>(p.status)->where = 3;
+          reinterpret_cast<WsHeader *>(p.status)->where = kSiteBatchedWait;
         }
       }
     }
@@ -522,10 +523,15 @@ __global__ void __launch_bounds__(kBT, 1) batched_kernel(BParams p) {
 
 // G[b][d] (and S[b]) = sum over the slices of the block partials, fixed order
 __global__ void batched_reduce(int m, int n, int64_t B, int BL, int slices, const double *gpart, int dual,
-                               int out_dtype, void *G, double *S) {
+                               int out_dtype, void *G, double *S, const int *status, int pieces, int64_t lo,
+                               int64_t hi) {
   const int d = blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t b = blockIdx.y;
   if (d > n || (d == n && (dual || !S))) return;
+  // the main pass did nothing when its plan key did not match: write nothing
+  const volatile WsHeader *wh = reinterpret_cast<const volatile WsHeader *>(status);
+  if (!(wh->plan_m == m && wh->plan_n == n && wh->plan_pieces == pieces && wh->plan_lo == lo && wh->plan_hi == hi))
+    return;
   const int g = (int)(b / BL), bl = (int)(b % BL);
   const size_t stride = (size_t)2 * (n + 2) * BL;
   const size_t off = (size_t)(dual ? (n + 2) * BL : 0) + (size_t)d * BL + bl;
@@ -675,7 +681,7 @@ int contract_batched(const BatchedArgs &a, cudaStream_t st) {
   bp.plan = plan;
   bp.gpart = reinterpret_cast<double *>(ws + sizeof(WsHeader) + plan_bytes);
   bp.status = reinterpret_cast<int *>(ws);
-  rc = plan_to_device(a.m, a.n, a.off_lo, a.off_hi, bp.pieces, 256, 1024, plan, st);
+  rc = plan_to_device(a.m, a.n, a.off_lo, a.off_hi, bp.pieces, 256, 1024, a.work, st);
   if (rc != TK_OK) return rc;
   if (a.storage == TK_F32) {
     rc = dual ? launch_ncol<float, true, 1>(bp, ncol, grid, smem, st)
@@ -688,7 +694,8 @@ int contract_batched(const BatchedArgs &a, cudaStream_t st) {
   }
   if (rc != TK_OK) return rc;
   dim3 rg((unsigned)((a.n + 1 + 127) / 128), (unsigned)a.B);
-  batched_reduce<<<rg, 128, 0, st>>>(a.m, a.n, a.B, BL, slices, bp.gpart, dual ? 1 : 0, a.vec_dtype, a.G, a.S);
+  batched_reduce<<<rg, 128, 0, st>>>(a.m, a.n, a.B, BL, slices, bp.gpart, dual ? 1 : 0, a.vec_dtype, a.G, a.S,
+                                     bp.status, bp.pieces, a.off_lo, a.off_hi);
   TK_CUDA_CHECK(cudaGetLastError());
   return TK_OK;
 }

@@ -2,6 +2,8 @@
 // range into row-aligned pieces (cached per workspace), the launch
 // configuration and the launch of the streaming kernel (tk_contract_impl.cuh,
 // whose last block sums the per-block partials in a fixed order).
+#include <stddef.h>
+
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -133,10 +135,23 @@ static std::mutex g_plan_mu;
 static std::map<PlanKey, std::vector<WarpPlan>> g_plans;
 static std::map<std::pair<int, const void *>, PlanKey> g_uploaded;
 
-// Make sure the plan for `key` sits in the workspace's plan region.
-static int ensure_plan(const PlanKey &key, void *plan_region, cudaStream_t st) {
+// Record in a workspace header which plan its plan region now holds (the
+// kernel checks the record against its launch parameters).
+static int write_plan_key(void *work, const PlanKey &key, cudaStream_t st) {
+  const WsHeader h = plan_key(key.m, key.n, key.lo, key.hi, key.pieces);
+  unsigned char *dst = reinterpret_cast<unsigned char *>(work) + offsetof(WsHeader, plan_m);
+  const size_t bytes = offsetof(WsHeader, pad) - offsetof(WsHeader, plan_m);
+  TK_CUDA_CHECK(cudaMemcpyAsync(dst, reinterpret_cast<const unsigned char *>(&h) + offsetof(WsHeader, plan_m), bytes,
+                                cudaMemcpyHostToDevice, st));
+  return TK_OK;
+}
+
+// Make sure the plan for `key` sits in the plan region of workspace `work`
+// (the region starts right after the 256-byte header).
+static int ensure_plan(const PlanKey &key, void *work, cudaStream_t st) {
   int dev = 0;
   TK_CUDA_CHECK(cudaGetDevice(&dev));
+  void *plan_region = reinterpret_cast<unsigned char *>(work) + sizeof(WsHeader);
   std::lock_guard<std::mutex> lk(g_plan_mu);
   auto up = g_uploaded.find({dev, plan_region});
   if (up != g_uploaded.end() && up->second == key) return TK_OK;
@@ -149,14 +164,24 @@ static int ensure_plan(const PlanKey &key, void *plan_region, cudaStream_t st) {
   }
   TK_CUDA_CHECK(cudaMemcpyAsync(plan_region, it->second.data(), it->second.size() * sizeof(WarpPlan),
                                 cudaMemcpyHostToDevice, st));
+  int rc = write_plan_key(work, key, st);
+  if (rc != TK_OK) return rc;
   g_uploaded[{dev, plan_region}] = key;
   return TK_OK;
 }
 
-int plan_to_device(int m, int n, int64_t lo, int64_t hi, int pieces, int row_cost, int tri_cost, void *region,
+int plan_to_device(int m, int n, int64_t lo, int64_t hi, int pieces, int row_cost, int tri_cost, void *work,
                    cudaStream_t st) {
   PlanKey key{m, n, lo, hi, pieces, row_cost, tri_cost};
-  return ensure_plan(key, region, st);
+  return ensure_plan(key, work, st);
+}
+
+void forget_plan(void *work) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  void *plan_region = reinterpret_cast<unsigned char *>(work) + sizeof(WsHeader);
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  g_uploaded.erase({dev, plan_region});
 }
 
 // ------------------------------------------------------------------ launch config
@@ -231,22 +256,11 @@ int contract_resolve(int m, int n, int storage, bool dual, tk_contract_config *o
   return TK_OK;
 }
 
-int contract_pass(const ContractArgs &a, int *grid_out, const double **part_out, cudaStream_t st) {
-  const bool dual = a.v != nullptr;
-  Resolved r;
-  int rc = resolve(a.m, a.n, a.storage, dual, &r);
-  if (rc != TK_OK) return rc;
-  DevInfo di;
-  dev_info(&di);
+// Launch parameters of one pass over the workspace or scratch region at
+// a.work (plan region after the header, partials after `plan_bytes`).
+static KParams make_kparams(const ContractArgs &a, const Resolved &r, int pieces, size_t plan_bytes) {
   unsigned char *ws = reinterpret_cast<unsigned char *>(a.work);
-  WarpPlan *plan = reinterpret_cast<WarpPlan *>(ws + sizeof(WsHeader));
-  double *part = reinterpret_cast<double *>(ws + sizeof(WsHeader) + contract_plan_bytes(di.sms));
-  const int pieces = r.ppw * r.grid * r.warps;
-  PlanKey key{a.m, a.n, a.off_lo, a.off_hi, pieces, r.row_cost, r.tri_cost};
-  rc = ensure_plan(key, plan, st);
-  if (rc != TK_OK) return rc;
   WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
-  TK_CUDA_CHECK(cudaMemsetAsync(&hdr->ticket, 0, sizeof(hdr->ticket) + sizeof(hdr->done), st));
   KParams kp;
   kp.m = a.m;
   kp.n = a.n;
@@ -257,15 +271,15 @@ int contract_pass(const ContractArgs &a, int *grid_out, const double **part_out,
   kp.alpha = a.alpha;
   kp.v = a.v;
   kp.vec_dtype = a.vec_dtype;
-  kp.part = part;
+  kp.part = reinterpret_cast<double *>(ws + sizeof(WsHeader) + plan_bytes);
   kp.status = a.status;
-  kp.plan = plan;
+  kp.plan = reinterpret_cast<const WarpPlan *>(ws + sizeof(WsHeader));
   kp.pieces = pieces;
   kp.ticket = &hdr->ticket;
   kp.done = &hdr->done;
   kp.dynamic = r.schedule == 2;
   kp.fin = a.fin;
-  kp.fin.part = part;
+  kp.fin.part = kp.part;
   kp.fin.grid = r.grid;
   kp.fin.m = a.m;
   kp.fin.n = a.n;
@@ -275,15 +289,37 @@ int contract_pass(const ContractArgs &a, int *grid_out, const double **part_out,
   kp.cap = r.cap;
   kp.vec_bytes = r.vec_bytes;
   kp.warp_bytes = r.warp_bytes;
-  if (grid_out) *grid_out = r.grid;
-  if (part_out) *part_out = part;
+  return kp;
+}
+
+static int launch_pass(const ContractArgs &a, const KParams &kp, const Resolved &r, bool dual, cudaStream_t st) {
+  WsHeader *hdr = reinterpret_cast<WsHeader *>(a.work);
+  TK_CUDA_CHECK(cudaMemsetAsync(&hdr->ticket, 0, sizeof(hdr->ticket) + sizeof(hdr->done), st));
   if (a.storage == TK_F64) return contract_launch_f64(kp, dual, r.nc, r.grid, r.warps * 32, r.smem, st);
   if (a.storage == TK_F32) return contract_launch_f32(kp, dual, r.nc, r.grid, r.warps * 32, r.smem, st);
   return contract_launch_bf16(kp, dual, r.nc, r.grid, r.warps * 32, r.smem, st);
 }
 
+int contract_pass(const ContractArgs &a, int *grid_out, const double **part_out, cudaStream_t st) {
+  const bool dual = a.v != nullptr;
+  Resolved r;
+  int rc = resolve(a.m, a.n, a.storage, dual, &r);
+  if (rc != TK_OK) return rc;
+  DevInfo di;
+  dev_info(&di);
+  const int pieces = r.ppw * r.grid * r.warps;
+  PlanKey key{a.m, a.n, a.off_lo, a.off_hi, pieces, r.row_cost, r.tri_cost};
+  rc = ensure_plan(key, a.work, st);
+  if (rc != TK_OK) return rc;
+  const KParams kp = make_kparams(a, r, pieces, contract_plan_bytes(di.sms));
+  if (grid_out) *grid_out = r.grid;
+  if (part_out) *part_out = kp.part;
+  return launch_pass(a, kp, r, dual, st);
+}
+
 int contract_pass_static(const ContractArgs &a, WarpPlan *host_plan, int host_cap, StaticPlanState *state,
-                         size_t scratch_bytes, int *grid_out, const double **part_out, cudaStream_t st) {
+                         size_t scratch_bytes, bool capturing, int *grid_out, const double **part_out,
+                         cudaStream_t st) {
   const bool dual = a.v != nullptr;
   Resolved r;
   int rc = resolve(a.m, a.n, a.storage, dual, &r);
@@ -294,52 +330,29 @@ int contract_pass_static(const ContractArgs &a, WarpPlan *host_plan, int host_ca
   if (pieces > host_cap || need > scratch_bytes)
     return fail(TK_ENOMEM, "contraction needs %zu bytes of scratch (%d plan records); the static scratch holds %zu",
                 need, pieces, scratch_bytes);
-  unsigned char *ws = reinterpret_cast<unsigned char *>(a.work);
-  WarpPlan *plan = reinterpret_cast<WarpPlan *>(ws + sizeof(WsHeader));
-  double *part = reinterpret_cast<double *>(ws + sizeof(WsHeader) + plan_bytes);
-  if (!(state->valid && state->m == a.m && state->n == a.n && state->lo == a.off_lo && state->hi == a.off_hi &&
-        state->pieces == pieces && state->rc == r.row_cost && state->tc == r.tri_cost)) {
+  const bool current = state->valid && state->m == a.m && state->n == a.n && state->lo == a.off_lo &&
+                       state->hi == a.off_hi && state->pieces == pieces && state->rc == r.row_cost &&
+                       state->tc == r.tri_cost;
+  if (!current) {
+    // re-planning copies from host memory and waits for the copy: neither
+    // may happen inside a stream capture, so refuse before touching the stream
+    if (capturing)
+      return fail(TK_EINVAL, "the static scratch holds no plan for m=%d, n=%d under the current launch "
+                  "configuration: make one call with this shape outside stream capture first", a.m, a.n);
     build_plan(a.m, a.n, a.off_lo, a.off_hi, pieces, r.row_cost, r.tri_cost, host_plan);
-    TK_CUDA_CHECK(cudaMemcpyAsync(plan, host_plan, plan_bytes, cudaMemcpyHostToDevice, st));
+    unsigned char *ws = reinterpret_cast<unsigned char *>(a.work);
+    TK_CUDA_CHECK(cudaMemcpyAsync(ws + sizeof(WsHeader), host_plan, plan_bytes, cudaMemcpyHostToDevice, st));
+    PlanKey key{a.m, a.n, a.off_lo, a.off_hi, pieces, r.row_cost, r.tri_cost};
+    rc = write_plan_key(a.work, key, st);
+    if (rc != TK_OK) return rc;
     // the host records are reused by the next rebuild: wait for the copy
     TK_CUDA_CHECK(cudaStreamSynchronize(st));
     *state = StaticPlanState{1, a.m, a.n, a.off_lo, a.off_hi, pieces, r.row_cost, r.tri_cost};
   }
-  WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
-  TK_CUDA_CHECK(cudaMemsetAsync(&hdr->ticket, 0, sizeof(hdr->ticket) + sizeof(hdr->done), st));
-  KParams kp;
-  kp.m = a.m;
-  kp.n = a.n;
-  kp.K = reinterpret_cast<const unsigned char *>(a.K);
-  kp.off_lo = a.off_lo;
-  kp.off_hi = a.off_hi;
-  kp.bytes = (a.off_hi - a.off_lo) * dtype_size(a.storage);
-  kp.alpha = a.alpha;
-  kp.v = a.v;
-  kp.vec_dtype = a.vec_dtype;
-  kp.part = part;
-  kp.status = a.status;
-  kp.plan = plan;
-  kp.pieces = pieces;
-  kp.ticket = &hdr->ticket;
-  kp.done = &hdr->done;
-  kp.dynamic = r.schedule == 2;
-  kp.fin = a.fin;
-  kp.fin.part = part;
-  kp.fin.grid = r.grid;
-  kp.fin.m = a.m;
-  kp.fin.n = a.n;
-  kp.warps = r.warps;
-  kp.nbuf = r.nbuf;
-  kp.buf_bytes = r.buf_bytes;
-  kp.cap = r.cap;
-  kp.vec_bytes = r.vec_bytes;
-  kp.warp_bytes = r.warp_bytes;
+  const KParams kp = make_kparams(a, r, pieces, plan_bytes);
   if (grid_out) *grid_out = r.grid;
-  if (part_out) *part_out = part;
-  if (a.storage == TK_F64) return contract_launch_f64(kp, dual, r.nc, r.grid, r.warps * 32, r.smem, st);
-  if (a.storage == TK_F32) return contract_launch_f32(kp, dual, r.nc, r.grid, r.warps * 32, r.smem, st);
-  return contract_launch_bf16(kp, dual, r.nc, r.grid, r.warps * 32, r.smem, st);
+  if (part_out) *part_out = kp.part;
+  return launch_pass(a, kp, r, dual, st);
 }
 
 

@@ -384,6 +384,24 @@ static __device__ void final_reduce(const FinalizeArgs &f, const double *part, i
   }
 }
 
+// Block-uniform check at kernel entry that the workspace header's plan key
+// is the launch's own (m, n, pieces, range); on a mismatch the status word
+// records TK_EINVAL at kSiteStalePlan and the caller returns before any load.
+__device__ __forceinline__ bool plan_is_stale(int *status, int m, int n, int pieces, int64_t lo, int64_t hi) {
+  __shared__ int s_stale;
+  if (threadIdx.x == 0) {
+    const volatile WsHeader *wh = reinterpret_cast<const volatile WsHeader *>(status);
+    s_stale = !(wh->plan_m == m && wh->plan_n == n && wh->plan_pieces == pieces && wh->plan_lo == lo &&
+                wh->plan_hi == hi);
+    if (s_stale) {
+      atomicExch(&reinterpret_cast<WsHeader *>(status)->status, TK_EINVAL);
+      reinterpret_cast<WsHeader *>(status)->where = kSiteStalePlan;
+    }
+  }
+  __syncthreads();
+  return s_stale != 0;
+}
+
 template <typename ST, typename CT, bool D, int NC>
 __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(KParams p) {
   using N = Nm<CT, D>;
@@ -404,6 +422,11 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
   const int gbytes = (int)((((D ? 2 : 1) * n * (int)sizeof(CT)) + 127) & ~127);
   unsigned char *bufs = wb + warp_fixed_bytes<CT, D>() + gbytes;
   const int NB = p.nbuf;
+
+  // the plan region must hold the plan of this launch (a CUDA graph replayed
+  // after a later call re-planned the region for another shape would read
+  // pieces of another layout): compare the key the host wrote with the upload
+  if (plan_is_stale(p.status, m, n, p.pieces, p.off_lo, p.off_hi)) return;
 
   // rows of a block that starts with a row of length L (rows shrink by one):
   // at most kRows, at most L, within `cap` entries
@@ -627,7 +650,7 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
     if (!__all_sync(0xffffffffu, mbar_wait_bounded(&hdr->bar[bi], parity))) {
       if (lane == 0) {
         atomicExch(&reinterpret_cast<WsHeader *>(p.status)->status, TK_ETIMEOUT);
-        reinterpret_cast<WsHeader *>(p.status)->where = 1;
+        reinterpret_cast<WsHeader *>(p.status)->where = kSiteContractWait;
       }
       failed = true;
       break;
@@ -850,7 +873,16 @@ inline int launch_nc(const KParams &kp, int grid, int threads, size_t smem, cuda
   auto kern = contract_kernel<ST, CT, D, NC>;
   if (threads > max_threads<CT, D, NC>())
     return fail(TK_EINVAL, "contract: %d threads exceed the kernel's bound", threads);
-  TK_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // raise the kernel's dynamic shared-memory limit once per device (and when
+  // a launch needs more): the attribute call is then absent from later calls,
+  // which a stream capture may record
+  static int limit_set[64] = {0};
+  int dev = 0;
+  TK_CUDA_CHECK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64 || limit_set[dev] < (int)smem) {
+    TK_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (dev >= 0 && dev < 64) limit_set[dev] = (int)smem;
+  }
   kern<<<grid, threads, smem, st>>>(kp);
   TK_CUDA_CHECK(cudaGetLastError());
   return TK_OK;

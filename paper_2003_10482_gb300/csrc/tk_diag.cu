@@ -21,7 +21,7 @@ __global__ void k_wait_nothing_arrives(int *status, long long budget_cycles) {
   if (threadIdx.x == 0) {
     if (!all_ok) {
       atomicExch(&reinterpret_cast<WsHeader *>(status)->status, TK_ETIMEOUT);
-      reinterpret_cast<WsHeader *>(status)->where = 9;
+      reinterpret_cast<WsHeader *>(status)->where = kSiteDiagWait;
     }
     mbar_arrive(&bar);  // complete the phase: the barrier is not left pending
   }

@@ -23,13 +23,33 @@ int cuda_fail(cudaError_t e, const char *what);
 // Layout of every workspace: a 256-byte header (status word and reserved
 // counters) followed by the per-block partial sums of the contraction.
 struct WsHeader {
-  int status;                 // TK_OK or TK_ETIMEOUT, set by kernels, read by tk_status_read
-  int where;                  // which wait ran out (diagnostic)
+  int status;                 // TK_OK, TK_ETIMEOUT or TK_EINVAL, set by kernels, read by tk_status_read
+  int where;                  // which check or wait failed (diagnostic; kSite* below)
   unsigned long long ticket;  // next piece of the contraction to hand out
   unsigned int done;          // blocks of the current pass that have written their partials
-  int pad[59];
+  // key of the work plan the plan region holds, written with every upload;
+  // the contraction kernel compares it with its own launch parameters and
+  // returns before any load when they differ (a CUDA graph replayed after a
+  // later call re-planned the region for another shape)
+  int plan_m, plan_n, plan_pieces;
+  long long plan_lo, plan_hi;
+  int pad[52];
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
+
+// where-codes of the status word
+enum { kSiteContractWait = 1, kSiteBatchedWait = 3, kSiteStalePlan = 4, kSiteDiagWait = 9 };
+
+// The key to write into a workspace header after its plan region was filled.
+inline WsHeader plan_key(int m, int n, int64_t lo, int64_t hi, int pieces) {
+  WsHeader h{};
+  h.plan_m = m;
+  h.plan_n = n;
+  h.plan_pieces = pieces;
+  h.plan_lo = lo;
+  h.plan_hi = hi;
+  return h;
+}
 
 // Work of one warp of the contraction: rows [start, end) (row-aligned
 // offsets); t[0..m-3] is the prefix Q of the first row, t[m-2] its c.
@@ -43,9 +63,15 @@ static_assert(sizeof(WarpPlan) == 48, "plan record");
 void build_plan(int m, int n, int64_t lo, int64_t hi, int pieces, int64_t row_cost, int64_t tri_cost,
                 WarpPlan *out);
 
-// Upload (once, cached per region) the cut of [lo, hi) into `pieces` pieces.
-int plan_to_device(int m, int n, int64_t lo, int64_t hi, int pieces, int row_cost, int tri_cost, void *region,
+// Upload (once, cached per workspace address) the cut of [lo, hi) into
+// `pieces` pieces into the plan region of workspace `work` (right after its
+// header) and record the plan's key in the header.
+int plan_to_device(int m, int n, int64_t lo, int64_t hi, int pieces, int row_cost, int tri_cost, void *work,
                    cudaStream_t st);
+// Drop the host's record of which plan the workspace at `work` holds (the
+// memory is about to hold something else, or is new memory at an address a
+// workspace used before).
+void forget_plan(void *work);
 
 // Batched contraction (one pass for B vectors); returns TK_EUNSUPPORTED when
 // the shape is outside what the batched kernel covers (callers then loop).
@@ -131,9 +157,12 @@ struct StaticPlanState {
 // Same pass as contract_pass, on a fixed scratch region of `scratch_bytes`
 // bytes (header, plan region, partials laid out as in a workspace).  The plan
 // is built into host_plan (capacity host_cap records; no host or device
-// allocation) and uploaded only when it differs from *state.
+// allocation) and uploaded only when it differs from *state; with
+// `capturing` set, a pass that would have to upload a plan is refused
+// (TK_EINVAL) before anything is issued on the stream.
 int contract_pass_static(const ContractArgs &a, WarpPlan *host_plan, int host_cap, StaticPlanState *state,
-                         size_t scratch_bytes, int *grid_out, const double **part_out, cudaStream_t st);
+                         size_t scratch_bytes, bool capturing, int *grid_out, const double **part_out,
+                         cudaStream_t st);
 
 // Bytes of the workspace regions (plan records for every warp of the largest
 // launch, then the per-block partial sums).

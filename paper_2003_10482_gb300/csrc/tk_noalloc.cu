@@ -33,11 +33,17 @@ static StaticPlanState g_plan_state[kNoAllocMaxDevices];
 static WarpPlan g_host_plan[kNoAllocPlanCap];
 static std::mutex g_noalloc_mu;
 
-static int scratch_for_current_device(void **out, int *dev_out) {
+// The device address of the array on the current device; the first call on
+// a device looks it up and zeroes the header (status word, plan key).  With
+// `capturing` set, a device whose array is not set up yet is refused before
+// anything is issued (the zeroing is a synchronous memset).
+static int scratch_for_current_device(bool capturing, void **out, int *dev_out) {
   int dev = 0;
   TK_CUDA_CHECK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(TK_EUNSUPPORTED, "device %d beyond %d", dev, kNoAllocMaxDevices);
   if (!g_scratch_dev[dev]) {
+    if (capturing)
+      return fail(TK_EINVAL, "tk_contract_noalloc: the first call on a device must come before any stream capture");
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
@@ -63,12 +69,15 @@ extern "C" int tk_contract_noalloc(int m, int64_t n, int storage, const void *K,
   if (((uintptr_t)K & 15u) != 0) return fail(TK_EINVAL, "K must be 16-byte aligned");
   const int64_t N = tk_packed_size(m, n);
   if (N < 0) return fail(TK_EOVERFLOW, "C(n+m-1, m) overflows");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  TK_CUDA_CHECK(cudaStreamIsCapturing(st, &cs));
+  const bool capturing = cs != cudaStreamCaptureStatusNone;
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
   void *scratch = nullptr;
   int dev = 0;
-  int rc = scratch_for_current_device(&scratch, &dev);
+  int rc = scratch_for_current_device(capturing, &scratch, &dev);
   if (rc != TK_OK) return rc;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   ContractArgs a;
   memset(&a, 0, sizeof(a));
   a.m = m;
@@ -88,6 +97,19 @@ extern "C" int tk_contract_noalloc(int m, int64_t n, int storage, const void *K,
   a.fin.S = S;
   int grid = 0;
   const double *part = nullptr;
-  return contract_pass_static(a, g_host_plan, kNoAllocPlanCap, &g_plan_state[dev], kNoAllocScratchBytes, &grid,
-                              &part, st);
+  return contract_pass_static(a, g_host_plan, kNoAllocPlanCap, &g_plan_state[dev], kNoAllocScratchBytes, capturing,
+                              &grid, &part, st);
+}
+
+extern "C" int tk_contract_noalloc_status(void *stream) {
+  int dev = 0;
+  TK_CUDA_CHECK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(TK_EUNSUPPORTED, "device %d beyond %d", dev, kNoAllocMaxDevices);
+  void *p = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    p = g_scratch_dev[dev];
+  }
+  if (!p) return TK_OK;  // no call has run on this device
+  return tk_status_read(p, stream);
 }

@@ -39,6 +39,50 @@ __global__ void k_predict(int t, int d, const double *Xt, int B, const double *W
   if (lane == 0) Y[b * t + j] = s;
 }
 
+// Adaptive threshold of Section 6.3: keep feature j of problem b when
+// |w_j| > 2 std(w), std the population standard deviation of the d weights.
+// One block per problem; mean and variance in FP64 by a two-pass sum in a
+// fixed order (thread-strided partials, then a fixed tree), so the decision
+// is reproducible.
+__global__ void __launch_bounds__(256) k_support(int d, const double *W, uint8_t *keep, int64_t *count) {
+  __shared__ double sh[256];
+  __shared__ int shc[256];
+  const double *w = W + (size_t)blockIdx.x * d;
+  auto block_sum = [&](double v) -> double {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    const double t = sh[0];
+    __syncthreads();
+    return t;
+  };
+  double s = 0.0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) s += w[j];
+  const double mean = block_sum(s) / d;
+  double q = 0.0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    const double e = w[j] - mean;
+    q += e * e;
+  }
+  const double thr = 2.0 * sqrt(block_sum(q) / d);
+  int c = 0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    const bool k = fabs(w[j]) > thr;
+    keep[(size_t)blockIdx.x * d + j] = k ? 1 : 0;
+    c += k;
+  }
+  shc[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) shc[threadIdx.x] += shc[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && count) count[blockIdx.x] = shc[0];
+}
+
 // SplitMix64 step: add the golden-ratio increment, then the variant-13 mixer
 static inline uint64_t splitmix64(uint64_t &st) {
   uint64_t z = (st += 0x9E3779B97F4A7C15ull);
@@ -97,5 +141,16 @@ extern "C" int tk_nystrom_select(int64_t N, int64_t np, uint64_t seed, int64_t *
     sorted.insert(std::upper_bound(sorted.begin(), sorted.end(), pick), pick);
   }
   std::copy(sorted.begin(), sorted.end(), out);
+  return TK_OK;
+}
+
+extern "C" int tk_support_threshold(int64_t d, int64_t B, const double *W, uint8_t *keep, int64_t *count,
+                                    void *stream) {
+  if (d < 1 || B < 0) return fail(TK_EINVAL, "bad sizes");
+  if (B == 0) return TK_OK;
+  if (!W || !keep) return fail(TK_EINVAL, "NULL pointer");
+  if (d > 2147483647ll || B > 2147483647ll) return fail(TK_EUNSUPPORTED, "sizes too large");
+  k_support<<<(unsigned)B, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>((int)d, W, keep, count);
+  TK_CUDA_CHECK(cudaGetLastError());
   return TK_OK;
 }

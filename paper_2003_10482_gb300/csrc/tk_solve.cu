@@ -190,6 +190,10 @@ struct Solver {
   int n, m;
   std::vector<double> h_a, h_b;  // coefficient staging
 
+  // the tensor the Hessian-vector passes read (the optional second copy)
+  const void *hvp_tensor() const { return P->K_hvp ? P->K_hvp : P->K; }
+  int hvp_storage() const { return P->K_hvp ? P->hvp_storage_dtype : P->storage_dtype; }
+
   // Objective (or HVP) of the problems in `list` only: their rows are gathered,
   // contracted as one smaller batch and the results scattered back; rows of
   // the other problems in F / grad / gn2 (or Hd) are left as they are.
@@ -220,7 +224,8 @@ struct Solver {
     k_gather<<<grid_for(nb * n), 256, 0, st>>>(nb, n, w.idx, A, w.Ac);
     k_gather<<<grid_for(nb * n), 256, 0, st>>>(nb, n, w.idx, d, w.dc);
     TK_CUDA_CHECK(cudaGetLastError());
-    rc = tk_contract(m, n, P->storage_dtype, P->K, nb, TK_F64, w.Ac, m - 2, w.dc, w.G, nullptr, w.cws, w.cws_bytes, st);
+    rc = tk_contract(m, n, hvp_storage(), hvp_tensor(), nb, TK_F64, w.Ac, m - 2, w.dc, w.G, nullptr, w.cws,
+                     w.cws_bytes, st);
     if (rc != TK_OK) return rc;
     k_hvp_finish_idx<<<grid_for(nb * n), 256, 0, st>>>(m, nb, n, w.idx, w.G, d, P->lambda, P->mask, Hd);
     TK_CUDA_CHECK(cudaGetLastError());
@@ -234,7 +239,8 @@ struct Solver {
     return TK_OK;
   }
   int hvp(const double *A, const double *d, double *Hd) {
-    int rc = tk_contract(m, n, P->storage_dtype, P->K, B, TK_F64, A, m - 2, d, w.G, nullptr, w.cws, w.cws_bytes, st);
+    int rc = tk_contract(m, n, hvp_storage(), hvp_tensor(), B, TK_F64, A, m - 2, d, w.G, nullptr, w.cws,
+                         w.cws_bytes, st);
     if (rc != TK_OK) return rc;
     k_hvp_finish<<<grid_for(B * n), 256, 0, st>>>(m, B, n, w.G, d, P->lambda, P->mask, Hd);
     TK_CUDA_CHECK(cudaGetLastError());
@@ -279,6 +285,20 @@ extern "C" size_t tk_solve_workspace_size(const tk_problem *P) {
   return solve_layout(P->B, P->n, cws, nullptr, nullptr);
 }
 
+extern "C" int tk_dual_hvp(int m, int64_t n, int storage, const void *K, int64_t B, const double *A, const double *V,
+                           const double *lambda, double *HV, void *work, size_t work_bytes, void *stream) {
+  if (B < 0) return fail(TK_EINVAL, "B < 0");
+  if (B == 0) return TK_OK;
+  if (!lambda || !HV || !V) return fail(TK_EINVAL, "NULL pointer");
+  // K[a^{m-2}, v] into HV, then HV = (m-1) HV + lambda v in place
+  int rc = tk_contract(m, n, storage, K, B, TK_F64, A, m - 2, V, HV, nullptr, work, work_bytes, stream);
+  if (rc != TK_OK) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  k_hvp_finish<<<grid_for(B * n), 256, 0, st>>>(m, B, (int)n, HV, V, lambda, nullptr, HV);
+  TK_CUDA_CHECK(cudaGetLastError());
+  return TK_OK;
+}
+
 #define TK_TRY(x)                  \
   do {                             \
     int rc__ = (x);                \
@@ -289,6 +309,8 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
                              size_t work_bytes, void *stream) {
   if (!P || !O || !A || !R || !work) return fail(TK_EINVAL, "NULL argument");
   if (P->B < 1 || !P->K || !P->y || !P->lambda) return fail(TK_EINVAL, "bad problem");
+  if (P->K_hvp && (P->hvp_storage_dtype < TK_F64 || P->hvp_storage_dtype > TK_BF16))
+    return fail(TK_EINVAL, "bad storage dtype %d of the Hessian-vector tensor", P->hvp_storage_dtype);
   if (O->method != TK_NEWTON_CG && O->method != TK_GD_BT) return fail(TK_EINVAL, "unknown method %d", O->method);
   if (O->max_iter < 0 || O->tol_gradnorm < 0 || O->tol_rel_gap < 0) return fail(TK_EINVAL, "bad options");
   const size_t need = tk_solve_workspace_size(P);

@@ -63,19 +63,46 @@ def accumulation_depth(n: int, warp_triangles: int) -> int:
 
 
 def contraction_bound(n: int, abs_terms: np.ndarray, storage: str, m: int, lo: int = 0, hi: int | None = None,
-                      dual: bool = False) -> np.ndarray:
+                      dual: bool = False, dynamic: bool = False) -> np.ndarray:
     """Entrywise bound on |computed - exact| for a contraction of an
-    already-rounded K: gamma_k * sum |terms| with k = accumulation_depth."""
-    k = accumulation_depth(n, max_warp_triangles(m, n, storage, lo, hi, dual))
+    already-rounded K: gamma_k * sum |terms| with k = accumulation_depth.
+    Under the shared-ticket schedule (dynamic) any warp may enter every
+    triangle of the range, so T_w is the range's triangle count."""
+    if dynamic:
+        tw = oracle.packed_size(m - 2, n) if m > 2 else 1
+    else:
+        tw = max_warp_triangles(m, n, storage, lo, hi, dual)
+    k = accumulation_depth(n, tw)
     if storage == "f64":
         return 2.0 * k * U64 * abs_terms + 1e-300
     return 1.01 * k * U32 * abs_terms + 1e-30
 
 
-def batched_bound(abs_terms: np.ndarray, storage: str, n: int) -> np.ndarray:
-    """The batched kernel flushes its FP32 partials to FP64 every 2048 rows:
-    gamma_k * sum |terms| with k = 2 max(n, 2048) + 64."""
-    k = 2 * max(n, 2048) + 64
-    if storage == "f64":
-        return 2.0 * k * U64 * abs_terms + 1e-300
+def batched_accumulation_depth(n: int, m: int, dual: bool = False) -> int:
+    """Longest chain of FP32 roundings on the way to one output of the batched
+    kernel (tk_batched.cu), read off its accumulation structure:
+
+    * a thread's column accumulator receives at most one add per row of the
+      block's slice (the entry's multiply-add, or the row's own epilogue for
+      its own column) and one per triangle entered (the prefix terms); it is
+      flushed to FP64 once 2048 rows have passed, checked after blocks of at
+      most 16 rows: <= 2 (2048 + 15) + 1 adds between flushes;
+    * a row dot: <= ceil(n/16) column terms in a thread, then the sum over the
+      16 warps; a triangle's T: <= ceil(n/16) rows per warp, then 16 warps;
+    * the products of a term: the FP64 -> FP32 conversions of its m-1 vector
+      factors, the prefix product, the multinomial and 1/m scalings, the
+      epilogue's few operations: <= 3m + 8;
+    * the dual-number (HVP) pass adds, per product, the add of the product
+      rule: <= 2m more.
+    Cross-slice sums are FP64."""
+    rows = 2048 + 16 - 1
+    per = -(-n // 16)
+    k = (2 * rows + 1) + 2 * (per + 16) + 3 * m + 8
+    return k + (2 * m if dual else 0)
+
+
+def batched_bound(abs_terms: np.ndarray, storage: str, n: int, m: int, dual: bool = False) -> np.ndarray:
+    """Entrywise bound on |computed - exact| for the batched kernel on an
+    already-rounded K: gamma_k * sum |terms| with k = batched_accumulation_depth."""
+    k = batched_accumulation_depth(n, m, dual)
     return 1.01 * k * U32 * abs_terms + 1e-30

@@ -74,3 +74,38 @@ def test_batched_energy_and_dual_objective():
         assert np.allclose(A.grad[b].cpu().numpy(), gr_ref, rtol=1e-10, atol=1e-10)
         assert float(F[b]) == pytest.approx(oracle.dual_objective(S_ref, A[b].detach().cpu().numpy(),
                                                                   y.cpu().numpy(), 0.5, m), rel=1e-10)
+
+
+def test_dual_objective_gradcheck_fp64():
+    # F = K[a^m]/m + lam/2 |a|^2 - <y, a>: value and gradient from tk_objective,
+    # Hessian-vector products from tk_dual_hvp, checked by finite differences
+    m, n, d = 4, 8, 3
+    X = synth.small_problem(m, n, d, salt=67)
+    K = tk.tk_build_packed(torch.tensor(X, device="cuda"), m, storage="f64")
+    y = torch.tensor(synth.alpha_like(n, salt=68), device="cuda")
+    a = torch.tensor(synth.alpha_like(n, salt=69, batch=2), device="cuda", requires_grad=True)
+    f = lambda x: tka.dual_objective(x, K, m, y, 0.3)
+    assert torch.autograd.gradcheck(f, (a,), eps=1e-6, atol=1e-8, rtol=1e-7)
+    assert torch.autograd.gradgradcheck(f, (a,), eps=1e-6, atol=1e-7, rtol=1e-6)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_dual_hvp_matches_oracle(storage):
+    m, n, d, B = 4, 23, 4, 3
+    X = synth.small_problem(m, n, d, salt=90)
+    K64 = oracle.build(X, m)
+    Kt = torch.from_numpy(K64).to(torch.float64 if storage == "f64" else torch.float32)
+    Kr = Kt.double().numpy()
+    A = synth.alpha_like(n, salt=91, batch=B)
+    V = synth.alpha_like(n, salt=92, batch=B)
+    lam = np.array([0.1, 1.0, 7.0])
+    HV = tk.tk_dual_hvp(Kt.cuda(), m, n, torch.tensor(A, device="cuda"), torch.tensor(V, device="cuda"),
+                        torch.tensor(lam, device="cuda")).cpu().numpy()
+    from gpu_util import contraction_bound
+    for b in range(B):
+        ref = (m - 1) * oracle.hvp(Kr, A[b], V[b], m) + lam[b] * V[b]
+        hab = (m - 1) * oracle.hvp(np.abs(Kr), np.abs(A[b]), np.abs(V[b]), m) + lam[b] * np.abs(V[b])
+        # the dual-number pass carries two accumulation chains; the finish is
+        # two FP64 operations
+        tol = 2 * contraction_bound(n, hab, storage, m, dual=True) + 4 * 2.0 ** -53 * hab
+        assert np.all(np.abs(HV[b] - ref) <= tol), float(np.max(np.abs(HV[b] - ref) / tol))

@@ -27,8 +27,9 @@ def test_tuned_single_vector_contraction_matches_oracle():
         G, S = tk.tk_contract(Kt.cuda(), m, n, torch.tensor(a, device="cuda"))
         g_ref, _ = oracle.contract(Kr, a, m)
         g_abs, _ = oracle.contract(np.abs(Kr), np.abs(a), m)
-        # the tuned schedule may be the shared-ticket one: allow a warp to enter every triangle
-        tol = contraction_bound(n, g_abs, "f32", m) * 4
+        # the tuned schedule may be the shared-ticket one, under which a warp
+        # may enter every triangle
+        tol = contraction_bound(n, g_abs, "f32", m, dynamic=True)
         assert np.all(np.abs(G.cpu().numpy() - g_ref) <= tol)
         assert autotune.apply("contract", m, n, "f32")
     finally:
@@ -51,6 +52,6 @@ def test_tuned_batched_contraction_matches_oracle():
         for b in (0, B // 2, B - 1):
             g_ref, _ = oracle.contract(Kr, A[b], m)
             g_abs, _ = oracle.contract(np.abs(Kr), np.abs(A[b]), m)
-            assert np.all(np.abs(G[b] - g_ref) <= 4 * batched_bound(g_abs, "f32", n))
+            assert np.all(np.abs(G[b] - g_ref) <= batched_bound(g_abs, "f32", n, m))
     finally:
         tk.tk_batched_set_config(reset=True)

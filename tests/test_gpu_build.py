@@ -46,11 +46,31 @@ def test_build_ranges_are_bit_identical():
     assert torch.equal(torch.cat(parts), full)
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
 @pytest.mark.parametrize("feat,deg", [("poly", 2), ("poly", 3), ("exp", 1)])
-def test_build_feature_maps(feat, deg):
+def test_build_feature_maps(feat, deg, storage):
+    # The epilogue maps the accumulated linear sum s_hat (|s_hat - s| <= e, the
+    # linear build's bound) through t -> t^deg (deg - 1 rounded products) or
+    # t -> exp(t) (CUDA's exp: at most 2 ulp in FP32, 1 ulp in FP64), then
+    # rounds to the storage type.  Propagated:
+    #   power: |s_hat^deg - s^deg| <= deg (|s| + e)^(deg-1) e,  plus (deg-1) u |K|
+    #   exp:   |exp(s_hat) - exp(s)| <= exp(s + e)(exp(e) - 1),  plus 4 u |K|
     m, n, d = 4, 12, 3
     X = 0.5 * synth.small_problem(m, n, d, salt=17)
     code = oracle.FEAT_POLY if feat == "poly" else oracle.FEAT_EXP
     K_ref = oracle.build(X, m, feat=code, degree=deg)
-    K = tk.tk_build_packed(torch.tensor(X, device="cuda"), m, storage="f64", feat=feat, degree=deg)
-    assert np.allclose(K.cpu().numpy(), K_ref, rtol=1e-12, atol=1e-14)
+    s_lin = oracle.build(X, m)
+    K_abs = oracle.build(np.abs(X), m)
+    K = tk.tk_build_packed(torch.tensor(X, device="cuda"), m, storage=storage, feat=feat, degree=deg)
+    Kh = as_f64(K)
+    u = U64 if storage == "f64" else U32
+    e = 1.01 * (d + m + 2) * u * K_abs
+    if feat == "poly":
+        tol = deg * (np.abs(s_lin) + e) ** (deg - 1) * e + 1.01 * (deg - 1) * u * np.abs(K_ref)
+    else:
+        tol = np.exp(s_lin + e) * np.expm1(e) + 4 * u * np.abs(K_ref)
+    if storage == "bf16":
+        tol = tol + UBF16 * (np.abs(Kh) + tol)
+    tol = tol + 1e-300
+    err = np.abs(Kh - K_ref)
+    assert np.all(err <= tol), float(np.max(err / tol))

@@ -1,0 +1,87 @@
+"""The Nystrom configuration end to end (Section 6.1 with the support read-out of
+Section 6.3): n' = 600 landmarks drawn uniformly without replacement from
+50,000 points (d = 200, rows ~ N(0, Sigma), Sigma_ij = 0.5^|i-j|), the packed
+m = 4 tensor over them, the dual solve, w = J_q(X^T a), prediction of 10,000
+held-out points.
+
+The FP64-storage solve is the reference.  Every other solution a is judged
+under the FP64 tensor: F is lambda-strongly convex, so for any a
+    F(a) - F* <= |grad F(a)|^2 / (2 lambda),
+which bounds F(a) - F(a_ref) from above by a's exact gradient and from below
+by the reference's.  BF16 storage alone makes the stored quartic form
+indefinite along the null space of X^T (600 landmarks > 200 features), so its
+own minimiser runs off; the mixed scheme reads the BF16 copy only in the
+Hessian-vector passes and the FP32 tensor for the objective and gradient,
+whose zero defines the solution."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+tk = pytest.importorskip("paper_2003_10482_gb300")
+
+REL_TARGET = 1e-6  # relative objective gap asked of the FP32-accuracy solves
+
+
+@pytest.fixture(scope="module")
+def nystrom():
+    c = synth.nystrom_bf16()
+    N = c["X_train"].shape[0]
+    idx = tk.tk_nystrom_select(N, c["n_prime"], c["select_seed"])
+    assert idx == list(oracle.nystrom_select(N, c["n_prime"], c["select_seed"]))
+    XL = torch.tensor(c["X_train"][idx], device="cuda")
+    yL = torch.tensor(c["y_train"][idx], device="cuda")
+    Xt = torch.tensor(c["X_test"], device="cuda")
+    m, n = c["m"], len(idx)
+    K = {s: tk.tk_build_packed(XL, m, storage=s) for s in ("f64", "f32", "bf16")}
+    lam = torch.tensor([c["lam"]], dtype=torch.float64, device="cuda")
+    t0 = time.perf_counter()
+    A64, rep64, rc64 = tk.tk_solve_dual(K["f64"], m, n, yL, lam, tol=0.0, rel_gap=1e-10, max_iter=60)
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t0
+    yield dict(c=c, m=m, n=n, XL=XL, yL=yL, Xt=Xt, K=K, lam=lam, A64=A64, rep64=rep64, t64=t64)
+    del K
+    torch.cuda.empty_cache()
+
+
+def _judge(nys, a):
+    """(F, |grad F|) of a under the FP64 tensor, test MSE, recovered support."""
+    m, n = nys["m"], nys["n"]
+    F, _, gn = tk.tk_objective(nys["K"]["f64"], m, n, a.contiguous(), nys["yL"], nys["lam"])
+    W = tk.tk_primal(nys["XL"], a, m)
+    yhat = tk.tk_predict(nys["Xt"], W).cpu().numpy().reshape(-1)
+    mse = float(np.mean((yhat - nys["c"]["y_test"]) ** 2))
+    return float(F[0]), float(gn[0]), mse, set(tk.support_threshold(W))
+
+
+@pytest.mark.parametrize("scheme", ["f32", "mixed_bf16_f32"])
+def test_nystrom_solution_matches_fp64(nystrom, scheme):
+    nys = nystrom
+    m, n, lam = nys["m"], nys["n"], float(nys["lam"][0])
+    K = nys["K"]
+    K_obj, K_hvp = (K["f32"], None) if scheme == "f32" else (K["f32"], K["bf16"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    A, rep, rc = tk.tk_solve_dual(K_obj, m, n, nys["yL"], nys["lam"], tol=0.0, rel_gap=1e-7, max_iter=40,
+                                  K_hvp=K_hvp)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    F_ref, g_ref, mse_ref, sup_ref = _judge(nys, nys["A64"][0])
+    F, g, mse, sup = _judge(nys, A[0])
+    print(f"\n{scheme}: {rep[0]['iters']} iterations, {rep[0]['passes']} passes, {secs:.2f} s "
+          f"(FP64 reference {nys['rep64'][0]['iters']} iterations, {nys['rep64'][0]['passes']} passes, "
+          f"{nys['t64']:.2f} s); F - F_ref = {F - F_ref:+.3e} (F_ref {F_ref:.9f}); "
+          f"MSE {mse:.6f} vs {mse_ref:.6f}; support {len(sup)} vs {len(sup_ref)}")
+    slack = 1e-12 * abs(F_ref)  # rounding of the FP64 objective itself
+    assert F - F_ref <= g * g / (2 * lam) + slack
+    assert F_ref - F <= g_ref * g_ref / (2 * lam) + slack
+    assert abs(F - F_ref) <= REL_TARGET * abs(F_ref)
+    true_sup = set(np.flatnonzero(nys["c"]["w_true"]).tolist())
+    assert sup == sup_ref and true_sup <= sup_ref  # the 2 std threshold finds all of w*'s support
+    assert abs(mse - mse_ref) <= 1e-3 * mse_ref

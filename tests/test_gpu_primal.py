@@ -42,3 +42,22 @@ def test_nystrom_pipeline_small():
     yref = oracle.predict(c["X_test"], oracle.primal_from_dual(XL, a_ref, 4))
     assert np.allclose(yhat, yref, rtol=1e-6, atol=1e-8)
     assert oracle.mse(yhat, c["y_test"]) == pytest.approx(oracle.mse(yref, c["y_test"]), rel=1e-6)
+
+
+@pytest.mark.parametrize("d,B", [(1, 1), (7, 3), (200, 2), (20_000, 1)])
+def test_support_threshold_matches_oracle(d, B):
+    # Section 6.3: keep |w_j| > 2 std(w); computed on the device in FP64.  The
+    # draws are heavy-tailed so that some weights pass and most do not.
+    rng = synth.rng_for(97, d)
+    W = rng.standard_normal((B, d)) ** 3
+    keep, cnt = tk.tk_support_threshold(torch.tensor(W, device="cuda"))
+    keep, cnt = keep.cpu().numpy(), cnt.cpu().numpy()
+    for b in range(B):
+        ref = oracle.threshold_support(W[b])
+        got = np.flatnonzero(keep[b])
+        # a weight within rounding of the threshold could go either way
+        thr = 2.0 * np.std(W[b])
+        near = np.abs(np.abs(W[b]) - thr) <= 1e-12 * max(thr, 1e-300)
+        assert set(got[~near[got]]) == set(ref[~near[ref]])
+        assert cnt[b] == got.size
+    assert tk.support_threshold(torch.tensor(W[0], device="cuda")) == list(np.flatnonzero(keep[0]))
