@@ -148,73 +148,119 @@ def _oracle_sample(target_s: float, max_entries: int = 40_000_000):
     oracle.contract(K0, a, m)
     rate = 100_000 / max(time.perf_counter() - t0, 1e-6)
     S = int(min(max(rate * target_s, 10_000), max_entries))
-    return oracle.build(X, m, 0, S), a, m
+    # the sample is built on every host thread (untimed setup)
+    import concurrent.futures as cf
+
+    import numpy as np
+    T = _host_threads()
+    cuts = [S * i // T for i in range(T + 1)]
+    with cf.ThreadPoolExecutor(max_workers=T) as ex:
+        parts = list(ex.map(lambda i: oracle.build(X, m, cuts[i], cuts[i + 1]), range(T)))
+    return np.concatenate(parts), a, m
 
 
-def _time_oracle(K, a, m):
+def _time_oracle(K, a, m, threads: int = 1):
+    """Wall time of the oracle's contraction of K (as it stands), on `threads`
+    host threads each contracting one contiguous chunk (the C oracle releases
+    the interpreter lock while it runs; the chunk sums are added afterwards)."""
+    import concurrent.futures as cf
+
     import oracle
     t0 = time.perf_counter()
-    oracle.contract(K, a, m)
+    if threads <= 1:
+        oracle.contract(K, a, m)
+    else:
+        N = K.shape[0]
+        cuts = [N * i // threads for i in range(threads + 1)]
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            parts = list(ex.map(lambda i: oracle.contract(K[cuts[i]:cuts[i + 1]], a, m, lo=cuts[i]),
+                                range(threads)))
+        g = sum(pp[0] for pp in parts)
+        S = sum(pp[1] for pp in parts)
+        del g, S
     return time.perf_counter() - t0
 
 
-def _sample_text(S):
+def _host_threads() -> int:
+    return len(os.sched_getaffinity(0))
+
+
+def _sample_text(S, threads):
     return (f"first {S:,} packed entries of the n=400 m=4 tensor (built by the oracle, untimed); "
-            f"FP64 oracle contraction K[a^3] and K[a^4], single thread; value = entries/s x 4 B "
-            f"(the FP32 storage the GPU streams)")
+            f"FP64 oracle contraction K[a^3] and K[a^4] on {threads} host thread(s), contiguous chunks; "
+            f"value = entries/s x 4 B (the FP32 storage the GPU streams)")
+
+
+def _config():
+    """The workload both arms report (the reference arm runs it on samples)."""
+    import math
+    N = math.comb(400 + 3, 4)
+    return {"workload": WORKLOAD, "m": 4, "n": 400, "d": 100, "storage": "f32", "packed_entries": N,
+            "packed_bytes": N * 4}
 
 
 def cpu_baseline_leg(target_s: float = 2.5) -> dict:
-    """The FP64 oracle's contraction, single-threaded, on a prefix of the
-    same packed tensor."""
+    """The FP64 oracle's contraction on a prefix of the same packed tensor, on
+    all host cores and on one; and the oracle's full dual solve of the plain
+    FP64 configuration."""
+    import oracle
+    import synth
     K, a, m = _oracle_sample(target_s)
-    dt = _time_oracle(K, a, m)
-    eps = K.shape[0] / dt
-    return {"value": eps * 4 / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": _sample_text(K.shape[0]), "entries_per_s": eps, "seconds": dt,
-            "host_cores": os.cpu_count(), "affinity_cores": len(os.sched_getaffinity(0))}
+    T = _host_threads()
+    dt1 = _time_oracle(K, a, m, 1)
+    dtT = _time_oracle(K, a, m, T)
+    c1 = synth.plain_fp64()
+    Kc1 = oracle.build(c1["X"], c1["m"])
+    t0 = time.perf_counter()
+    _, info = oracle.solve_dual_newton(Kc1, c1["y"], c1["lam"], c1["m"], tol=1e-10)
+    solve_s = time.perf_counter() - t0
+    return {"value": K.shape[0] / dtT * 4 / 1e9, "unit": "GB/s", "cores": T, "kind": "oracle",
+            "sample": _sample_text(K.shape[0], T), "entries_per_s": K.shape[0] / dtT, "seconds": dtT,
+            "single_thread": {"value": K.shape[0] / dt1 * 4 / 1e9, "unit": "GB/s", "seconds": dt1},
+            "host_cores": os.cpu_count(), "affinity_cores": T,
+            "oracle_solve_plain_fp64": {"seconds": solve_s, "newton_iterations": info["iters"],
+                                        "gradnorm": info["gradnorm"],
+                                        "workload": "plain FP64: m=4, n=40, d=10, dense-Hessian Newton to 1e-10"}}
 
 
 def run_reference(args) -> None:
-    """Reference arm: the oracle on the host cores, one bounded sample per step,
+    """Reference arm: the oracle on all host cores, one bounded sample per step,
     the whole run sized to about half a minute of timed work."""
     rank = _env_int("RANK", 0)
     if rank != 0:
         return
     steps = max(args.steps, 1)
-    K, a, m = _oracle_sample(max(0.02, 30.0 / steps))
+    T = _host_threads()
+    K, a, m = _oracle_sample(max(0.02, 30.0 * T / steps))
     for _ in range(args.warmup):
-        _time_oracle(K[: max(1, K.shape[0] // 10)], a, m)
-    times = [_time_oracle(K, a, m) for _ in range(steps)]
+        _time_oracle(K[: max(1, K.shape[0] // 10)], a, m, T)
+    times = [_time_oracle(K, a, m, T) for _ in range(steps)]
     per = statistics.mean(times)
     v = K.shape[0] / per * 4 / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
             "steps": steps, "warmup": args.warmup, "ms_per_step": 1000.0 * per,
             "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD, "m": 4, "n": 400, "d": 100, "storage": "oracle f64"},
-            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                             "sample": _sample_text(K.shape[0])},
+            "data": "synthetic", "config": _config(),
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": T, "kind": "oracle",
+                             "sample": _sample_text(K.shape[0], T)},
             "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def batched_leg(dev) -> dict:
-    """Dual solves/s of the batched FP32 path against plain FP64 solves.
+    """Dual solves/s of the batched FP32 path against plain FP64 solves, on the
+    whole lambda path.
 
     Workload: m = 4, n' = 300 Nystrom landmarks (uniform without replacement,
-    tk_nystrom_select) of 20,000 points, d = 80; the lambda path is
-    logspace(-4, 0, 64) x 8 cross-validation folds (masks).  Timed here: the
-    10 largest lambdas (0.27 <= lambda <= 1) x 8 folds = 80 problems, where
-    the FP32 tensor resolves the objective to within 1e-6 of the FP64 optimum
-    (for smaller lambda the dual variables grow like |y_perp| / lambda and
-    K[a^4] cancels beyond FP32: 1e-4 at lambda = 0.11; beyond FP64 near
-    lambda = 1e-4).  Both arms run Newton-CG
-    to the same relative-gap target (1e-7) with the same 40-iteration cap:
-    batched = one tk_solve_dual call over the 80 problems on the FP32 tensor
-    (one pass serves the whole batch); plain = one FP64-tensor solve per
-    problem, timed on 8 of them.  Accuracy: F of each batched solution under
-    the FP64 tensor against the plain FP64 solve's F."""
+    tk_nystrom_select) of 20,000 points, d = 80; lambda in logspace(-4, 0, 64)
+    x 8 cross-validation folds (masks) = 512 problems.  Both arms use the
+    full-Hessian Newton method (one Hessian pass per problem and iteration,
+    FP64 Cholesky on the device) to the same relative-gap target (1e-7) with
+    the same 40-iteration cap: batched = one tk_solve_dual call over all 512
+    problems on the FP32 tensor; plain = one call per problem on the FP64
+    tensor, for every problem.  Accuracy: F of each batched solution under the
+    FP64 tensor against that problem's plain FP64 solve; reported per lambda
+    (worst fold), with each problem's status and passes."""
     import torch
 
     import paper_2003_10482_gb300 as tk
@@ -225,52 +271,108 @@ def batched_leg(dev) -> dict:
     X = torch.tensor(p["X"][idx], device=dev)
     y = torch.tensor(p["y"][idx], device=dev)
     n = X.shape[0]
-    sel = torch.arange(432, 512, device=dev)  # lambda indices 54..63, all folds
-    lam = torch.tensor(p["lambdas"], device=dev)[sel].contiguous()
-    mask = torch.tensor(p["masks"], device=dev)[sel].contiguous()
+    lam = torch.tensor(p["lambdas"], device=dev)
+    mask = torch.tensor(p["masks"], device=dev)
+    B = lam.numel()
     K32 = tk.tk_build_packed(X, m, storage="f32")
     K64 = tk.tk_build_packed(X, m, storage="f64")
     gap, iters = 1e-7, 40
-    # batch width per lane, staging tile, buffers, slices and the batched /
-    # single-vector crossover, chosen by measurement on the Hessian-vector
-    # product (most passes of a Newton-CG solve are HVPs); untimed
-    from paper_2003_10482_gb300 import autotune
-    tuned = autotune.tune_batched(K32, m, n, int(lam.numel()), dual=True, reps=2)
-    tk.tk_solve_dual(K32, m, n, y, lam[:32], mask=mask[:32], tol=0.0, rel_gap=gap, max_iter=2)  # warm-up
-    tk.tk_solve_dual(K64, m, n, y, lam[:1], mask=mask[:1], tol=0.0, rel_gap=gap, max_iter=2)
+    # warm-up (library load, plans, workspaces)
+    tk.tk_solve_dual(K32, m, n, y, lam[:2], mask=mask[:2], method="newton_full", tol=0.0, rel_gap=gap, max_iter=1)
+    tk.tk_solve_dual(K64, m, n, y, lam[:1], mask=mask[:1], method="newton_full", tol=0.0, rel_gap=gap, max_iter=1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    A32, rep, _ = tk.tk_solve_dual(K32, m, n, y, lam, mask=mask, tol=0.0, rel_gap=gap, max_iter=iters)
+    A32, rep, _ = tk.tk_solve_dual(K32, m, n, y, lam, mask=mask, method="newton_full", tol=0.0, rel_gap=gap,
+                                   max_iter=iters)
     torch.cuda.synchronize()
     t_batched = time.perf_counter() - t0
-    B = lam.numel()
-    sample = list(range(0, B, B // 8))[:8]  # 8 of the problems, spread over lambda and folds
-    t_plain, errs, per_lambda = [], [], []
-    for j in sample:
+    t_plain, F64, rep64 = 0.0, [], []
+    for j in range(B):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        A64, r64, _ = tk.tk_solve_dual(K64, m, n, y, lam[j:j + 1], mask=mask[j:j + 1], tol=0.0, rel_gap=gap,
-                                       max_iter=iters)
+        _, r64, _ = tk.tk_solve_dual(K64, m, n, y, lam[j:j + 1], mask=mask[j:j + 1], method="newton_full",
+                                     tol=0.0, rel_gap=gap, max_iter=iters)
         torch.cuda.synchronize()
-        t_plain.append(time.perf_counter() - t0)
-        F, _, _ = tk.tk_objective(K64, m, n, A32[j].contiguous(), y, lam[j:j + 1])
-        e = abs(float(F[0]) - r64[0]["F"]) / abs(r64[0]["F"])
-        errs.append(e)
-        per_lambda.append({"lambda": float(lam[j]), "rel_obj_diff": e, "fp64_passes": r64[0]["passes"],
-                           "batched_passes": rep[j]["passes"]})
+        t_plain += time.perf_counter() - t0
+        F64.append(r64[0]["F"])
+        rep64.append(r64[0])
+    # every batched solution judged under the FP64 tensor
+    Fb, _, _ = tk.tk_objective(K64, m, n, A32.contiguous(), y, lam)
+    Fb = Fb.cpu().numpy()
+    errs = [abs(float(Fb[j]) - F64[j]) / max(abs(F64[j]), 1e-300) for j in range(B)]
+    per_lambda = []
+    lam_h = p["lambdas"]
+    for i in range(0, B, 8):
+        js = range(i, i + 8)
+        per_lambda.append({"lambda": float(lam_h[i]),
+                           "max_rel_obj_diff_vs_fp64": max(errs[j] for j in js),
+                           "fp32_converged": sum(rep[j]["status"] == 0 for j in js),
+                           "fp64_converged": sum(rep64[j]["status"] == 0 for j in js),
+                           "fp32_passes_max": max(rep[j]["passes"] for j in js),
+                           "fp64_passes_max": max(rep64[j]["passes"] for j in js)})
+    ok = [j for j in range(B) if errs[j] <= 1e-6]
     held_out = float(A32[~mask.bool()].abs().max()) if bool((~mask.bool()).any()) else 0.0
-    plain_s = statistics.mean(t_plain)
-    tk.tk_batched_set_config(reset=True)
-    return {"workload": "batched_path_m4_np300_d80 (lambda in [0.27, 1] x 8 folds)", "problems": B,
+    return {"workload": "batched_path_m4_np300_d80: 64 lambdas in [1e-4, 1] x 8 folds = 512 problems",
+            "problems": B, "method": "newton_full (Hessian pass + FP64 Cholesky per problem and iteration)",
             "batched_fp32": {"solves_per_s": B / t_batched, "seconds": t_batched,
                              "converged": sum(r["status"] == 0 for r in rep),
+                             "passes_total": sum(r["passes"] for r in rep),
                              "max_passes": max(r["passes"] for r in rep)},
-            "plain_fp64": {"solves_per_s": 1.0 / plain_s, "seconds_per_solve": plain_s, "timed_problems": len(sample)},
-            "speedup": (B / t_batched) * plain_s,
+            "plain_fp64": {"solves_per_s": B / t_plain, "seconds": t_plain, "timed_problems": B,
+                           "converged": sum(r["status"] == 0 for r in rep64),
+                           "passes_total": sum(r["passes"] for r in rep64)},
+            "speedup": (B / t_batched) / (B / t_plain),
             "target": "relative objective gap 1e-7 (Newton decrement), at most 40 Newton iterations",
-            "autotuned": {"config": tuned["best"], "hvp_ms": tuned["ms"], "candidates": len(tuned["trials"])},
+            "within_1e-6_of_fp64": len(ok),
             "max_rel_obj_diff_vs_fp64": max(errs), "held_out_max_abs_alpha": held_out,
             "per_lambda": per_lambda}
+
+
+def dexter_leg(dev) -> dict:
+    """The Dexter-shaped workload (few points, very many sparse features): the
+    packed build (d-heavy: 2d flops per entry) and a full dual solve, timed;
+    the solution checked against the linear kernel's closed-form gradient."""
+    import numpy as np
+    import torch
+
+    import paper_2003_10482_gb300 as tk
+    import synth
+    p = synth.dexter_like()
+    m, Xh, yh, lam = p["m"], p["X"], p["y"], p["lam"]
+    n, d = Xh.shape
+    X = torch.tensor(Xh, device=dev)
+    y = torch.tensor(yh, device=dev)
+    tk.tk_build_packed(X[:8], m, storage="f32")  # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    K = tk.tk_build_packed(X, m, storage="f32")
+    e1.record()
+    torch.cuda.synchronize()
+    build_ms = e0.elapsed_time(e1)
+    out = {"workload": f"dexter_like_m4_n{n}_d{d} (0.5 % dense features, FP32 storage)",
+           "packed_entries": int(K.numel()), "build_ms": build_ms,
+           "build_tflops_at_2d_flop_per_entry": 2 * d * K.numel() / build_ms / 1e9}
+    for method in ("newton_full", "newton_cg"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        A, rep, rc = tk.tk_solve_dual(K, m, n, y, [lam], method=method, tol=1e-6, max_iter=100)
+        torch.cuda.synchronize()
+        a = A[0].cpu().numpy()
+        u = Xh.T @ a
+        g_exact = float(np.linalg.norm(Xh @ u ** (m - 1) + lam * a - yh))
+        out[method] = {"solve_s": time.perf_counter() - t0, "iterations": rep[0]["iters"],
+                       "passes": rep[0]["passes"], "gradnorm": rep[0]["gradnorm"],
+                       "closed_form_gradnorm": g_exact, "status": rep[0]["status"]}
+    return out
+
+
+def peaks_leg() -> dict:
+    """Measured vector multiply-add rates (the denominators of the rooflines of
+    the kernels bound by vector arithmetic)."""
+    import paper_2003_10482_gb300 as tk
+    return {"fp32_simt_tflops": tk.tk_fma_probe("f32", iters=1 << 16) / 1e12,
+            "fp64_simt_tflops": tk.tk_fma_probe("f64", iters=1 << 12) / 1e12,
+            "how": "tk_fma_probe: 8 x SMs blocks of 256 threads, 16 independent FMA chains each, CUDA events, best of 3"}
 
 
 def run_ours(args) -> None:
@@ -385,16 +487,18 @@ def run_ours(args) -> None:
         achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
         traffic = _profile_traffic(alg_bytes) if npts == p["X"].shape[0] else None
         cfg = tk.tk_contract_get_config(m, n, "f32")
+        cfg_line = _config() if npts == p["X"].shape[0] else {
+            "workload": workload, "m": m, "n": n, "d": int(X.shape[1]), "storage": "f32", "packed_entries": N,
+            "packed_bytes": bytes_all}
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload, "m": m, "n": n, "d": int(X.shape[1]), "storage": "f32",
-                       "packed_entries": N, "packed_bytes": bytes_all,
-                       "step": "tk_objective: one streaming pass (K[a^3], K[a^4]) + FP64 F/grad/|grad|",
-                       "l2": "inputs (4.33 GB) larger than L2 (129 MB); no flush",
-                       "parallelism": f"packed-range shards x{world}" if world > 1 else "1 GPU",
-                       "launch": cfg},
+            "config": cfg_line,
+            "setup": {"step": "tk_objective: one streaming pass (K[a^3], K[a^4]) + FP64 F/grad/|grad|",
+                      "l2": "inputs (4.33 GB) larger than L2 (129 MB); no flush",
+                      "parallelism": f"packed-range shards x{world}" if world > 1 else "1 GPU",
+                      "launch": cfg},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": f"{peak_kind} copy bandwidth",
@@ -413,7 +517,9 @@ def run_ours(args) -> None:
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_leg()
         if world == 1 and not args.no_batched:
+            line["peaks"] = peaks_leg()
             line["batched"] = batched_leg(dev)
+            line["dexter_shaped"] = dexter_leg(dev)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

@@ -64,7 +64,7 @@ enum { TK_F64 = 0, TK_F32 = 1, TK_BF16 = 2 };
 enum { TK_FEAT_LINEAR = 0, TK_FEAT_POLY = 1, TK_FEAT_EXP = 2 };
 
 /* Dual solver methods (the thesis does not state its algorithm). */
-enum { TK_NEWTON_CG = 0, TK_GD_BT = 1 };
+enum { TK_NEWTON_CG = 0, TK_GD_BT = 1, TK_NEWTON_FULL = 2 };
 
 /* Largest supported order and point count of the device contraction. */
 #define TK_MAX_ORDER 8
@@ -281,6 +281,15 @@ int tk_status_read(void *work, void *stream);
  * timeout path can be tested without faulting or hanging the device. */
 int tk_check_bounded_wait(void *work, size_t work_bytes, long long budget_cycles, void *stream);
 
+/* Diagnostic: the FP32 or FP64 multiply-add rate of the device's vector
+ * units.  Launches `blocks` blocks of 256 threads, each thread running 16
+ * independent multiply-add chains for `iters` rounds: 2 * 16 * iters * 256 *
+ * blocks floating-point operations, which the caller divides by the time it
+ * measures (CUDA events on `stream`).  out: `blocks` values of dtype (device).
+ * The rate is the denominator of the rooflines of the kernels bound by
+ * vector arithmetic rather than memory (build, batched contraction). */
+int tk_fma_probe(int dtype, int blocks, long long iters, void *out, void *stream);
+
 /* ------------------------------------------------------------ dual objective */
 
 /* Dual objective and gradient (Section 4, eqs. dual_tensor_kernel and jq, with
@@ -327,6 +336,22 @@ int tk_assemble_objective(int m, int64_t n, int64_t B, const double *G, const do
 int tk_dual_hvp(int m, int64_t n, int storage_dtype, const void *K, int64_t B, const double *A,
                 const double *V, const double *lambda, double *HV, void *work, size_t work_bytes,
                 void *stream);
+
+/* The full Hessian of the tensor term (Section 4, second derivative of
+ * eq. dual_tensor_kernel divided by m(m-1)):
+ *   H[i][j] = K[a^{m-2}]_{ij} = sum over i_3..i_m of K_{i,j,i_3..i_m} a_{i_3}...a_{i_m},
+ * a dense symmetric n x n FP64 matrix (row-major, device), from one pass over
+ * the packed tensor (each entry read once).  a: n FP64 (device).  Arithmetic
+ * as in tk_contract (FP32 with FP64 cross-block sums for FP32/BF16 storage);
+ * the few entries whose rows and columns are both prefix values
+ * (i, j <= the triangle's last prefix value) are summed with FP64 atomic
+ * adds, so they may vary in the last bits from run to run.  n up to 768
+ * (FP32/BF16 storage) or 384 (FP64 storage), else TK_EUNSUPPORTED.
+ * Workspace: tk_hessian_workspace_size bytes, which carry a cached work plan
+ * like the contraction's. */
+size_t tk_hessian_workspace_size(int m, int64_t n);
+int tk_hessian(int m, int64_t n, int storage_dtype, const void *K, const double *alpha, double *H, void *work,
+               size_t work_bytes, void *stream);
 
 /* ------------------------------------------------------------ primal side */
 
@@ -383,15 +408,20 @@ typedef struct {
 } tk_problem;
 
 typedef struct {
-    int method;             /* TK_NEWTON_CG (default) or TK_GD_BT */
+    int method;             /* TK_NEWTON_CG (default), TK_GD_BT or TK_NEWTON_FULL */
     double tol_gradnorm;    /* stop a problem when |grad F|_2 <= tol */
     int max_iter;           /* outer iterations */
     int max_cg;             /* conjugate-gradient steps per Newton step */
     double armijo_c;        /* sufficient-decrease constant (0: 1e-4) */
-    double tol_rel_gap;     /* Newton-CG: also stop a problem when its Newton decrement
-                               estimate -<grad F, p>/2 (p the inner-solve direction,
+    double tol_rel_gap;     /* Newton methods: also stop a problem when its Newton
+                               decrement estimate -<grad F, p>/2 (p the Newton direction,
                                F(a) - F* to second order) is <= tol_rel_gap * max(1, |F|);
                                0 = off */
+    int start_on_y;         /* 1: ignore A_inout's values and start each problem at the
+                               minimiser of F along the ray s y_b (y_b = y on its kept
+                               points): F(s y_b) = s^m K[y_b^m]/m + (lambda_b/2) s^2 |y_b|^2
+                               - s |y_b|^2, one contraction pass for K[y_b^m], then the
+                               positive root of its derivative; 0: start from A_inout */
 } tk_solve_opts;
 
 typedef struct {
@@ -402,11 +432,17 @@ typedef struct {
     int status;             /* TK_OK, TK_ENOTCONV (max_iter or no further decrease possible) */
 } tk_solve_report;
 
-/* Bytes of workspace tk_solve_dual needs. */
+/* Bytes of workspace tk_solve_dual needs with TK_NEWTON_CG or TK_GD_BT. */
 size_t tk_solve_workspace_size(const tk_problem *P);
 
+/* Bytes of workspace tk_solve_dual needs with the method of O (TK_NEWTON_FULL
+ * adds the Hessian pass's workspace and the Newton systems of up to 64
+ * problems). */
+size_t tk_solve_workspace_size_opts(const tk_problem *P, const tk_solve_opts *O);
+
 /* Solves the B problems from the starting points in A_inout (B x n FP64,
- * device; masked entries are zeroed), in FP64 vector arithmetic on the device:
+ * device; masked entries are zeroed), in FP64 vector arithmetic on the device
+ * (workspace: tk_solve_workspace_size_opts bytes):
  *   Newton-CG:  H p = -grad F by conjugate gradients with forcing term
  *               min(0.5, sqrt|grad F|), H v = (m-1) K[a^{m-2}, v] + lambda v,
  *               then backtracking (halving the step) until either Armijo's
@@ -414,6 +450,12 @@ size_t tk_solve_workspace_size(const tk_problem *P);
  *               convex along the line, so the latter certifies F(a + t p) <=
  *               F(a) from gradients alone when F's rounding noise hides the
  *               decrease);
+ *   NEWTON_FULL: p = -H^{-1} grad F with the full H = (m-1) K[a^{m-2}] +
+ *               lambda I on the kept points, from one Hessian pass per problem
+ *               (tk_hessian, reading K_hvp when given) and an FP64 Cholesky
+ *               factorisation on the device; the same backtracking; a problem
+ *               whose H is not positive definite (a rounded tensor) takes the
+ *               steepest-descent direction that iteration;
  *   GD_BT:      steepest descent with Armijo backtracking, step initialised
  *               from the previous accepted step.
  * Every objective is one contraction pass and every H v one dual-number pass

@@ -22,7 +22,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libtk.so")
 TK_OK, TK_EINVAL, TK_EOVERFLOW, TK_ENOMEM, TK_ECUDA, TK_ENOTCONV, TK_ETIMEOUT, TK_EUNSUPPORTED = range(8)
 TK_F64, TK_F32, TK_BF16 = 0, 1, 2
 TK_FEAT_LINEAR, TK_FEAT_POLY, TK_FEAT_EXP = 0, 1, 2
-TK_NEWTON_CG, TK_GD_BT = 0, 1
+TK_NEWTON_CG, TK_GD_BT, TK_NEWTON_FULL = 0, 1, 2
+_METHODS = {"newton_cg": TK_NEWTON_CG, "gd_bt": TK_GD_BT, "newton_full": TK_NEWTON_FULL}
 
 _DT = {torch.float64: TK_F64, torch.float32: TK_F32, torch.bfloat16: TK_BF16}
 _TORCH = {TK_F64: torch.float64, TK_F32: torch.float32, TK_BF16: torch.bfloat16}
@@ -88,6 +89,10 @@ def _declare(L):
         "tk_dual_hvp": (i32, [i32, i64, i32, P, i64, P, P, P, P, P, sz, P]),
         "tk_support_threshold": (i32, [i64, i64, P, P, P, P]),
         "tk_solve_workspace_size": (sz, [P]),
+        "tk_solve_workspace_size_opts": (sz, [P, P]),
+        "tk_hessian_workspace_size": (sz, [i32, i64]),
+        "tk_hessian": (i32, [i32, i64, i32, P, P, P, P, sz, P]),
+        "tk_fma_probe": (i32, [i32, i32, ctypes.c_longlong, P, P]),
         "tk_primal": (i32, [i32, i64, i64, P, i64, P, P, P]),
         "tk_predict": (i32, [i64, i64, P, i64, P, P, P]),
         "tk_nystrom_select": (i32, [i64, i64, u64, P]),
@@ -251,6 +256,27 @@ def tk_check_bounded_wait(work: torch.Tensor, budget_cycles: int = 1 << 22, stre
     """Run the library's bounded device wait on a barrier nothing arrives on
     (diagnostic); the status word of `work` then reads TK_ETIMEOUT."""
     _check(lib().tk_check_bounded_wait(_p(work), work.numel(), budget_cycles, _stream(stream)))
+
+
+def tk_fma_probe(dtype="f32", blocks: int = 0, iters: int = 1 << 16, reps: int = 3) -> float:
+    """Measured multiply-add rate of the vector units (FLOP/s) for FP32 or FP64:
+    the library's probe kernel timed with CUDA events (best of `reps`)."""
+    dev = torch.cuda.current_device()
+    if blocks <= 0:
+        blocks = 8 * torch.cuda.get_device_properties(dev).multi_processor_count
+    code = dtype_code(dtype)
+    out = torch.empty(blocks, dtype=_TORCH[code], device="cuda")
+    st = torch.cuda.current_stream()
+    _check(lib().tk_fma_probe(code, blocks, iters, _p(out), _stream(st)))  # warm-up
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        _check(lib().tk_fma_probe(code, blocks, iters, _p(out), _stream(st)))
+        e1.record(st)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e-3)
+    return 2.0 * 16 * iters * 256 * blocks / best
 
 
 def tk_status_read(work: torch.Tensor, stream=None) -> int:
@@ -422,7 +448,8 @@ class tk_problem(ctypes.Structure):
 
 class tk_solve_opts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("tol_gradnorm", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("max_cg", ctypes.c_int), ("armijo_c", ctypes.c_double), ("tol_rel_gap", ctypes.c_double)]
+                ("max_cg", ctypes.c_int), ("armijo_c", ctypes.c_double), ("tol_rel_gap", ctypes.c_double),
+                ("start_on_y", ctypes.c_int)]
 
 
 class tk_solve_report(ctypes.Structure):
@@ -436,12 +463,14 @@ _solve_ws: dict = {}
 def tk_solve_dual(K: torch.Tensor, m: int, n: int, y: torch.Tensor, lam, alpha0: torch.Tensor | None = None,
                   mask: torch.Tensor | None = None, method: str = "newton_cg", tol: float = 1e-10,
                   max_iter: int = 100, max_cg: int = 0, rel_gap: float = 0.0, K_hvp: torch.Tensor | None = None,
-                  stream=None):
+                  start_on_y: bool | None = None, stream=None):
     """Solve B dual problems over the packed tensor K.  Returns (alpha (B x n FP64),
     reports (list of dicts), rc) where rc is TK_OK or TK_ENOTCONV.  A problem
     stops when |grad F| <= tol or (Newton-CG, rel_gap > 0) when its Newton
     decrement estimate of F - F* is <= rel_gap * max(1, |F|).  K_hvp: an optional
-    lower-precision copy of K that only the Hessian-vector passes read."""
+    lower-precision copy of K that only the Hessian-vector passes read.  start_on_y:
+    start each problem at the minimiser of F along s*y (one extra pass; the default
+    for method="newton_full" when alpha0 is None)."""
     dev = K.device
     lam_t = torch.as_tensor(lam, dtype=torch.float64, device=dev).reshape(-1).contiguous()
     B = lam_t.numel()
@@ -452,8 +481,10 @@ def tk_solve_dual(K: torch.Tensor, m: int, n: int, y: torch.Tensor, lam, alpha0:
     prob = tk_problem(m, n, dtype_code(K.dtype), K.data_ptr(), yd.data_ptr(), B, lam_t.data_ptr(),
                       0 if mk is None else mk.data_ptr(), 0 if K_hvp is None else K_hvp.data_ptr(),
                       0 if K_hvp is None else dtype_code(K_hvp.dtype))
-    opts = tk_solve_opts(TK_NEWTON_CG if method == "newton_cg" else TK_GD_BT, tol, max_iter, max_cg, 0.0, rel_gap)
-    need = int(lib().tk_solve_workspace_size(ctypes.byref(prob)))
+    if start_on_y is None:
+        start_on_y = alpha0 is None and method == "newton_full"
+    opts = tk_solve_opts(_METHODS[method], tol, max_iter, max_cg, 0.0, rel_gap, int(bool(start_on_y)))
+    need = int(lib().tk_solve_workspace_size_opts(ctypes.byref(prob), ctypes.byref(opts)))
     if need == 0:
         raise TKError(TK_EINVAL, lib().tk_last_error().decode())
     key = dev.index
@@ -468,6 +499,28 @@ def tk_solve_dual(K: torch.Tensor, m: int, n: int, y: torch.Tensor, lam, alpha0:
         _check(rc)
     out = [{f: getattr(r, f) for f, _ in r._fields_} for r in reps]
     return A, out, rc
+
+
+_hess_ws: dict = {}
+
+
+def tk_hessian(K: torch.Tensor, m: int, n: int, alpha: torch.Tensor, H: torch.Tensor | None = None,
+               stream=None) -> torch.Tensor:
+    """K[alpha^{m-2}] as a dense symmetric n x n FP64 matrix, from one pass over K."""
+    a = alpha.reshape(n).to(torch.float64).contiguous()
+    if H is None:
+        H = torch.empty(n, n, dtype=torch.float64, device=a.device)
+    dev = a.device
+    with torch.cuda.device(dev):
+        need = int(lib().tk_hessian_workspace_size(m, n))
+    if need == 0:
+        raise TKError(TK_EINVAL, lib().tk_last_error().decode())
+    ws = _hess_ws.get(dev.index)
+    if ws is None or ws.numel() < need:
+        ws = new_workspace(need, dev)
+        _hess_ws[dev.index] = ws
+    _check(lib().tk_hessian(m, n, dtype_code(K.dtype), _p(K), _p(a), _p(H), _p(ws), ws.numel(), _stream(stream)))
+    return H
 
 
 def tk_primal(X: torch.Tensor, A: torch.Tensor, m: int, stream=None) -> torch.Tensor:

@@ -117,7 +117,7 @@ __device__ __forceinline__ double ld_k<float, double>(const unsigned char *K, in
 
 template <typename ST, typename CT>
 __global__ void __launch_bounds__(kHW * 32) hess_kernel(HParams p) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int m = p.m, n = p.n;
   if (plan_is_stale(p.status, m, n, p.pieces, -1, -1)) return;

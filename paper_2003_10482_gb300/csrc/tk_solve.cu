@@ -14,6 +14,18 @@
 
 namespace tk {
 
+size_t newton_ws_bytes(int n, int64_t nb);
+int newton_directions(int m, int n, int nb, const int *idx_dev, const double *Hk, const double *lambda,
+                      const uint8_t *mask, const double *grad, double *p, void *ws, int *bad_host,
+                      cudaStream_t st);
+int objective_from_hessian(int m, int n, int nb, const int *idx_dev, const double *Hk, const double *A,
+                           const double *y, const double *lambda, const uint8_t *mask, double *F, double *grad,
+                           double *gn2, cudaStream_t st);
+int take_hessians(int64_t B, int n, const double *flag_dev, const double *Hsrc, double *Hdst, cudaStream_t st);
+
+// problems whose Newton systems are formed and factorised together
+constexpr int kNewtonChunk = 64;
+
 // ------------------------------------------------------------------ kernels
 __global__ void k_mask(int64_t B, int n, const uint8_t *mask, double *x) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -42,6 +54,12 @@ __global__ void __launch_bounds__(256) k_dots(int n, const double *x, const doub
   for (int i = threadIdx.x; i < n; i += blockDim.x) s += x[b * n + i] * y[b * n + i];
   s = block_sum_fixed<256>(s, sh);
   if (threadIdx.x == 0) out[b] = s;
+}
+
+// x_b = y for every problem b
+__global__ void k_fill_y(int64_t B, int n, const double *y, double *x) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < B * n) x[i] = y[i % n];
 }
 
 // z_b = ca_b x_b + cb_b y_b  (z may alias x or y)
@@ -194,6 +212,25 @@ struct Solver {
   const void *hvp_tensor() const { return P->K_hvp ? P->K_hvp : P->K; }
   int hvp_storage() const { return P->K_hvp ? P->hvp_storage_dtype : P->storage_dtype; }
 
+  // full-Hessian Newton: every objective evaluation is a Hessian pass at the
+  // point (K[a^{m-1}] = K[a^{m-2}] a and K[a^m] = a . K[a^{m-1}]), whose
+  // matrices land in hdst (B x n x n, by problem) for the next Newton system
+  bool full = false;
+  double *hdst = nullptr;
+  unsigned char *hws = nullptr;
+  size_t hws_bytes = 0;
+  int *hidx = nullptr;  // device list of problems (B ints)
+  int hess_objective(const std::vector<int> &list, const double *A, double *F, double *grad, double *gn2) {
+    if (list.empty()) return TK_OK;
+    for (int b : list) {
+      int rc = tk_hessian(m, n, P->storage_dtype, P->K, A + (size_t)b * n, hdst + (size_t)b * n * n, hws, hws_bytes,
+                          st);
+      if (rc != TK_OK) return rc;
+    }
+    TK_CUDA_CHECK(cudaMemcpyAsync(hidx, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    return objective_from_hessian(m, n, (int)list.size(), hidx, hdst, A, P->y, P->lambda, P->mask, F, grad, gn2, st);
+  }
+
   // Objective (or HVP) of the problems in `list` only: their rows are gathered,
   // contracted as one smaller batch and the results scattered back; rows of
   // the other problems in F / grad / gn2 (or Hd) are left as they are.
@@ -202,6 +239,7 @@ struct Solver {
     return TK_OK;
   }
   int objective_sub(const std::vector<int> &list, const double *A, double *F, double *grad, double *gn2) {
+    if (full) return hess_objective(list, A, F, grad, gn2);
     const int64_t nb = (int64_t)list.size();
     if (nb == 0) return TK_OK;
     if (nb == B) return objective(A, F, grad, gn2);
@@ -232,6 +270,11 @@ struct Solver {
     return TK_OK;
   }
   int objective(const double *A, double *F, double *grad, double *gn2) {
+    if (full) {
+      std::vector<int> all(B);
+      for (int64_t b = 0; b < B; ++b) all[b] = (int)b;
+      return hess_objective(all, A, F, grad, gn2);
+    }
     int rc = tk_contract(m, n, P->storage_dtype, P->K, B, TK_F64, A, m - 1, nullptr, w.G, w.S, w.cws, w.cws_bytes, st);
     if (rc != TK_OK) return rc;
     k_assemble<<<(unsigned)B, 256, 0, st>>>(m, n, w.G, w.S, A, P->y, P->lambda, P->mask, F, grad, gn2);
@@ -285,6 +328,42 @@ extern "C" size_t tk_solve_workspace_size(const tk_problem *P) {
   return solve_layout(P->B, P->n, cws, nullptr, nullptr);
 }
 
+// extra bytes of the full-Hessian Newton method, after the common layout:
+// the Hessian pass's workspace, K[a^{m-2}] of every problem at its current
+// point and at its trial point, the Newton matrices and factors of one chunk
+// of problems, the device list of problems
+struct FullLayout {
+  size_t hws, hcur, htrial, nws, hidx, total;
+};
+static FullLayout full_layout(const tk_problem *P) {
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  FullLayout L{};
+  const size_t hws = tk_hessian_workspace_size(P->m, P->n);
+  if (hws == 0) return L;
+  const size_t mats = al((size_t)P->B * P->n * P->n * sizeof(double));
+  size_t off = 0;
+  L.hws = off;
+  off += al(hws);
+  L.hcur = off;
+  off += mats;
+  L.htrial = off;
+  off += mats;
+  L.nws = off;
+  off += al(newton_ws_bytes((int)P->n, std::min<int64_t>(P->B, kNewtonChunk)));
+  L.hidx = off;
+  off += al((size_t)P->B * sizeof(int));
+  L.total = off;
+  return L;
+}
+
+extern "C" size_t tk_solve_workspace_size_opts(const tk_problem *P, const tk_solve_opts *O) {
+  const size_t base = tk_solve_workspace_size(P);
+  if (base == 0 || !O) return base;
+  if (O->method != TK_NEWTON_FULL) return base;
+  const size_t extra = full_layout(P).total;
+  return extra == 0 ? 0 : ((base + 255) & ~size_t(255)) + extra;
+}
+
 extern "C" int tk_dual_hvp(int m, int64_t n, int storage, const void *K, int64_t B, const double *A, const double *V,
                            const double *lambda, double *HV, void *work, size_t work_bytes, void *stream) {
   if (B < 0) return fail(TK_EINVAL, "B < 0");
@@ -299,6 +378,27 @@ extern "C" int tk_dual_hvp(int m, int64_t n, int storage, const void *K, int64_t
   return TK_OK;
 }
 
+// Next trial step after a rejected one: the minimiser of the cubic that
+// matches F and its slope along p at 0 and at t (Hermite interpolation; the
+// form of Nocedal and Wright, Numerical Optimization, eq. 3.59), kept in
+// [0.1 t, 0.5 t]; halving when the cubic gives no usable minimiser.  Along a
+// Newton direction F is a polynomial of degree m in the step, which the cubic
+// follows far more closely than halving does.
+static double backtrack_step(double t, double f0, double g0, double f1, double g1) {
+  const double d1 = g0 + g1 - 3.0 * (f1 - f0) / t;
+  const double disc = d1 * d1 - g0 * g1;
+  double tn = 0.5 * t;
+  if (std::isfinite(disc) && disc >= 0.0 && std::isfinite(f1) && std::isfinite(g1)) {
+    const double d2 = sqrt(disc);
+    const double den = g1 - g0 + 2.0 * d2;
+    if (den != 0.0) {
+      const double c = t - t * (g1 + d2 - d1) / den;
+      if (std::isfinite(c)) tn = c;
+    }
+  }
+  return std::min(0.5 * t, std::max(0.1 * t, tn));
+}
+
 #define TK_TRY(x)                  \
   do {                             \
     int rc__ = (x);                \
@@ -311,9 +411,10 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
   if (P->B < 1 || !P->K || !P->y || !P->lambda) return fail(TK_EINVAL, "bad problem");
   if (P->K_hvp && (P->hvp_storage_dtype < TK_F64 || P->hvp_storage_dtype > TK_BF16))
     return fail(TK_EINVAL, "bad storage dtype %d of the Hessian-vector tensor", P->hvp_storage_dtype);
-  if (O->method != TK_NEWTON_CG && O->method != TK_GD_BT) return fail(TK_EINVAL, "unknown method %d", O->method);
+  if (O->method != TK_NEWTON_CG && O->method != TK_GD_BT && O->method != TK_NEWTON_FULL)
+    return fail(TK_EINVAL, "unknown method %d", O->method);
   if (O->max_iter < 0 || O->tol_gradnorm < 0 || O->tol_rel_gap < 0) return fail(TK_EINVAL, "bad options");
-  const size_t need = tk_solve_workspace_size(P);
+  const size_t need = tk_solve_workspace_size_opts(P, O);
   if (need == 0) return TK_EINVAL;
   if (work_bytes < need) return fail(TK_ENOMEM, "workspace %zu < %zu bytes", work_bytes, need);
   Solver s;
@@ -328,6 +429,22 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
   const double c_arm = O->armijo_c > 0 ? O->armijo_c : 1e-4;
   const int max_cg = O->max_cg > 0 ? O->max_cg : std::max(1, std::min(n, 200));
   const double tol = O->tol_gradnorm;
+  const bool newton = O->method == TK_NEWTON_CG || O->method == TK_NEWTON_FULL;
+  // full-Hessian Newton buffers (after the common layout)
+  double *Hcur = nullptr, *Htrial = nullptr;
+  unsigned char *nws = nullptr;
+  if (O->method == TK_NEWTON_FULL) {
+    unsigned char *base = reinterpret_cast<unsigned char *>(work) + ((tk_solve_workspace_size(P) + 255) & ~size_t(255));
+    const FullLayout L = full_layout(P);
+    s.full = true;
+    s.hws = base + L.hws;
+    s.hws_bytes = L.hcur - L.hws;
+    Hcur = reinterpret_cast<double *>(base + L.hcur);
+    Htrial = reinterpret_cast<double *>(base + L.htrial);
+    nws = base + L.nws;
+    s.hidx = reinterpret_cast<int *>(base + L.hidx);
+    s.hdst = Hcur;
+  }
 
   std::vector<double> F(B), gn2(B), Ft(B), gn2t(B), rr(B), rr_new(B), dHd(B), slope(B), slope_t(B), t(B), gstep(B, 0.0);
   // stall detection: best gradient norm so far and iterations since it last fell by 0.1 %
@@ -342,7 +459,41 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
   // (FP32/BF16) stored tensor can show it -- its form is indefinite at the iterate
   std::vector<char> indefinite(B, 0);
 
-  if (P->mask) {
+  if (O->start_on_y) {
+    // a_b = s_b y_b with s_b = argmin_s F(s y_b): F along the ray is the
+    // polynomial s^m S_b/m + lambda_b s^2 |y_b|^2 / 2 - s |y_b|^2 with
+    // S_b = K[y_b^m] from one contraction pass; its derivative
+    // S_b s^{m-1} + (lambda_b s - 1)|y_b|^2 rises from -|y_b|^2 at 0 to
+    // S_b / lambda_b^{m-1} >= 0 at 1/lambda_b (m even), so bisection finds the root
+    k_fill_y<<<grid_for(B * n), 256, 0, s.st>>>(B, n, P->y, A);
+    TK_CUDA_CHECK(cudaGetLastError());
+    if (P->mask) {
+      k_mask<<<grid_for(B * n), 256, 0, s.st>>>(B, n, P->mask, A);
+      TK_CUDA_CHECK(cudaGetLastError());
+    }
+    TK_TRY(tk_contract(s.m, n, P->storage_dtype, P->K, B, TK_F64, A, s.m - 1, nullptr, s.w.G, s.w.S, s.w.cws,
+                       s.w.cws_bytes, s.st));
+    for (auto &x : passes) ++x;
+    std::vector<double> Sy(B), yy(B), lam(B), sc(B), zero_b(B, 0.0);
+    TK_TRY(s.fetch(s.w.S, Sy));
+    TK_TRY(s.dots(A, A, yy));
+    TK_CUDA_CHECK(cudaMemcpyAsync(lam.data(), P->lambda, B * sizeof(double), cudaMemcpyDeviceToHost, s.st));
+    TK_CUDA_CHECK(cudaStreamSynchronize(s.st));
+    for (int64_t b = 0; b < B; ++b) {
+      double lo = 0.0, hi = 1.0 / lam[b];
+      if (!(yy[b] > 0.0) || !(lam[b] > 0.0)) {
+        sc[b] = 0.0;
+        continue;
+      }
+      for (int k = 0; k < 200; ++k) {
+        const double mid = 0.5 * (lo + hi);
+        const double d = Sy[b] * pow(mid, s.m - 1) + (lam[b] * mid - 1.0) * yy[b];
+        if (d < 0.0) lo = mid; else hi = mid;
+      }
+      sc[b] = 0.5 * (lo + hi);
+    }
+    TK_TRY(s.axpby(sc, A, zero_b, A, A));
+  } else if (P->mask) {
     k_mask<<<grid_for(B * n), 256, 0, s.st>>>(B, n, P->mask, A);
     TK_CUDA_CHECK(cudaGetLastError());
   }
@@ -405,6 +556,29 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
         TK_TRY(s.axpby(one, s.w.r, cb, s.w.d, s.w.d));
       }
       for (int64_t b = 0; b < B; ++b) t[b] = 1.0;
+    } else if (O->method == TK_NEWTON_FULL) {
+      // p = -H^{-1} g with H = (m-1) K[a^{m-2}] + lambda I from the Hessian pass
+      // that evaluated the current point; systems factorised in chunks
+      std::vector<int> list;
+      for (int64_t b = 0; b < B; ++b)
+        if (active[b]) list.push_back((int)b);
+      TK_TRY(s.axpby(zero, s.w.g, zero, s.w.g, s.w.p));
+      std::vector<double> bad_flag(B, 0.0);
+      for (size_t c0 = 0; c0 < list.size(); c0 += kNewtonChunk) {
+        const int nb = (int)std::min<size_t>(kNewtonChunk, list.size() - c0);
+        TK_CUDA_CHECK(cudaMemcpyAsync(s.hidx, list.data() + c0, nb * sizeof(int), cudaMemcpyHostToDevice, s.st));
+        std::vector<int> bad(nb, 0);
+        TK_TRY(newton_directions(s.m, n, nb, s.hidx, Hcur, P->lambda, P->mask, s.w.g, s.w.p, nws, bad.data(), s.st));
+        for (int j = 0; j < nb; ++j)
+          if (bad[j]) {
+            bad_flag[list[c0 + j]] = 1.0;
+            indefinite[list[c0 + j]] = 1;
+          }
+      }
+      // a form that is not positive definite (rounded tensor): steepest descent
+      TK_TRY(s.axpby(minus1, s.w.g, zero, s.w.g, s.w.at));
+      TK_TRY(s.select(bad_flag, s.w.at, s.w.p));
+      for (int64_t b = 0; b < B; ++b) t[b] = 1.0;
     } else {
       TK_TRY(s.axpby(minus1, s.w.g, zero, s.w.g, s.w.p));
       for (int64_t b = 0; b < B; ++b) t[b] = gstep[b] > 0 ? 2.0 * gstep[b] : 1.0 / std::max(1.0, sqrt(gn2[b]));
@@ -414,7 +588,7 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
       if (active[b] && !(slope[b] < 0)) {
         // not a descent direction (rounding in the inner solve): fall back to -grad
         slope[b] = -gn2[b];
-      } else if (active[b] && O->method == TK_NEWTON_CG && O->tol_rel_gap > 0 &&
+      } else if (active[b] && newton && O->tol_rel_gap > 0 &&
                  -0.5 * slope[b] <= O->tol_rel_gap * std::max(1.0, fabs(F[b]))) {
         // Newton decrement: F - F* ~ -<g, p>/2 is below the relative tolerance
         active[b] = 0;
@@ -423,11 +597,12 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
       }
     }
     // directions of problems whose slope was repaired: p = -g
-    for (int64_t b = 0; b < B; ++b) flag[b] = (active[b] && slope[b] == -gn2[b] && O->method == TK_NEWTON_CG) ? 1.0 : 0.0;
+    for (int64_t b = 0; b < B; ++b) flag[b] = (active[b] && slope[b] == -gn2[b] && newton) ? 1.0 : 0.0;
     TK_TRY(s.axpby(minus1, s.w.g, zero, s.w.g, s.w.at));
     TK_TRY(s.select(flag, s.w.at, s.w.p));
 
     // Armijo backtracking, all problems in lockstep
+    s.hdst = Htrial;
     std::vector<char> ls(B);
     std::vector<double> accepted(B, 0.0);
     std::vector<char> real_decrease(B, 0);  // accepted by Armijo's test (a decrease F's rounding cannot fake)
@@ -464,7 +639,7 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
           accepted[b] = 1.0;
           real_decrease[b] = armijo && Ft[b] < F[b] - 1e-12 * std::max(1.0, fabs(F[b]));
         } else {
-          t[b] *= 0.5;
+          t[b] = backtrack_step(t[b], F[b], slope[b], Ft[b], slope_t[b]);
           if (t[b] < 1e-30) {
             ls[b] = 0;
             stalled[b] = 1;
@@ -480,6 +655,12 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
     // take the accepted trial points (and their objective and gradient)
     TK_TRY(s.select(accepted, s.w.at, A));
     TK_TRY(s.select(accepted, s.w.gt, s.w.g));
+    if (s.full) {
+      // the accepted points' Hessians become the current ones (s.w.ca holds
+      // the accepted flags the selects just uploaded)
+      TK_TRY(take_hessians(B, n, s.w.ca, Htrial, Hcur, s.st));
+      s.hdst = Hcur;
+    }
     for (int64_t b = 0; b < B; ++b) {
       if (accepted[b] != 0.0) {
         F[b] = Ft[b];

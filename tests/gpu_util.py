@@ -106,3 +106,18 @@ def batched_bound(abs_terms: np.ndarray, storage: str, n: int, m: int, dual: boo
     already-rounded K: gamma_k * sum |terms| with k = batched_accumulation_depth."""
     k = batched_accumulation_depth(n, m, dual)
     return 1.01 * k * U32 * abs_terms + 1e-30
+
+
+def hessian_bound(n: int, m: int, abs_terms: np.ndarray, storage: str) -> np.ndarray:
+    """Entrywise bound on |computed - exact| for tk_hessian on an
+    already-rounded K: gamma_k * sum |terms| with k the longest chain of
+    roundings in the pass (tk_hessian.cu): a prefix-value table entry adds
+    once per triangle of its work item (at most every triangle,
+    C(n+m-3, m-2)); the term-A registers at most 64 triangles before an FP64
+    flush; a row part 5 shuffle levels, a column part 4 rows and 8 warps; the
+    products of a term (vector conversions, prefix products, weights) at most
+    3m + 8.  Item slots are summed in FP64."""
+    tri = oracle.packed_size(m - 2, n) if m > 2 else 1
+    k = max(tri, 64) + 5 + 12 + 3 * m + 8
+    u = U64 if storage == "f64" else U32
+    return 1.01 * k * u * abs_terms + 1e-300
