@@ -201,13 +201,19 @@ int tk_contract_get_config(int m, int64_t n, int storage_dtype, int dual, tk_con
  *   slice_mult   blocks per group of vectors = slice_mult * SMs / groups (1 or 2)
  *   min_batch    smallest B that takes the batched kernel (below it the
  *                single-vector pass runs once per vector); 0 = 28 (16 for
- *                r = m-2); a value sets both */
+ *                r = m-2); a value sets both
+ *   tensor_cores the tensor-core pass for r = m-1 (tcgen05.mma, TF32 with a
+ *                3-term split; the whole tensor, FP32 or BF16 storage,
+ *                n <= 320): 0 = where it pays (m = 3 or 4, n >= 64, B >= 128),
+ *                1 = wherever it covers the call, -1 = never.  In the result of
+ *                tk_batched_get_config: 1 when the call would take it, else 0 */
 typedef struct {
     int vpl;
     int block_bytes;
     int nbuf;
     int slice_mult;
     int min_batch;
+    int tensor_cores;
 } tk_batched_config;
 
 /* Sets the process-wide batched configuration (NULL restores the defaults).
@@ -289,6 +295,19 @@ int tk_check_bounded_wait(void *work, size_t work_bytes, long long budget_cycles
  * The rate is the denominator of the rooflines of the kernels bound by
  * vector arithmetic rather than memory (build, batched contraction). */
 int tk_fma_probe(int dtype, int blocks, long long iters, void *out, void *stream);
+
+/* Diagnostic of the tensor-core building blocks: one 128 x n_cols tile
+ * D = A B^T by tcgen05.mma (kind::tf32, FP32 accumulation in tensor memory),
+ * the operands staged in the K-major 128-byte-swizzled shared-memory layout
+ * the tensor-core kernels use; split = 1 carries each operand as two TF32
+ * parts (x = hi + lo) and sums hi*hi' + hi*lo' + lo*hi', which keeps about
+ * 2^-21 relative accuracy per product.  A: 128 x k, B: n_cols x k, D: 128 x
+ * n_cols, FP32 row-major (device); k = 32 or 64; n_cols a multiple of 16 in
+ * [16, 256].  work: at least the 256-byte header (a timed-out wait on the
+ * MMA's completion is reported by tk_status_read as TK_ETIMEOUT).  One block,
+ * asynchronous on `stream`.  TK_EUNSUPPORTED on a device without tcgen05. */
+int tk_umma_probe(int n_cols, int k, int split, const float *A, const float *B, float *D, void *work,
+                  size_t work_bytes, void *stream);
 
 /* ------------------------------------------------------------ dual objective */
 
@@ -400,10 +419,11 @@ typedef struct {
     const uint8_t *mask;    /* B x n, 1 = point kept, 0 = held out (device); NULL = all kept */
     const void *K_hvp;      /* optional second copy of the same tensor (N entries of
                                hvp_storage_dtype, device) that the Hessian-vector passes of
-                               Newton-CG read instead of K; NULL = K.  The objective and
-                               gradient (which fix the minimiser) always read K, so a
-                               BF16 copy here halves the bytes of most passes while the
-                               solution stays that of K's precision */
+                               Newton-CG and the Hessian passes of NEWTON_FULL read instead
+                               of K; NULL = K.  The objective and gradient (which fix the
+                               minimiser) always read K, so a lower-precision copy here
+                               cheapens most passes while the solution stays that of K's
+                               precision */
     int hvp_storage_dtype;
 } tk_problem;
 
@@ -451,13 +471,20 @@ size_t tk_solve_workspace_size_opts(const tk_problem *P, const tk_solve_opts *O)
  *               F(a) from gradients alone when F's rounding noise hides the
  *               decrease);
  *   NEWTON_FULL: p = -H^{-1} grad F with the full H = (m-1) K[a^{m-2}] +
- *               lambda I on the kept points, from one Hessian pass per problem
- *               (tk_hessian, reading K_hvp when given) and an FP64 Cholesky
- *               factorisation on the device; the same backtracking; a problem
+ *               lambda I on the kept points and an FP64 Cholesky factorisation
+ *               on the device.  Without K_hvp every evaluation of a point is
+ *               one Hessian pass over K (tk_hessian), which by Euler's identity
+ *               (K[a^{m-1}] = K[a^{m-2}] a, K[a^m] = a . K[a^{m-1}]) also gives F
+ *               and grad F, so an accepted step costs one pass; with K_hvp the
+ *               evaluations are contraction passes over K and each new point's
+ *               Hessian is one pass over K_hvp.  The same backtracking; a problem
  *               whose H is not positive definite (a rounded tensor) takes the
  *               steepest-descent direction that iteration;
  *   GD_BT:      steepest descent with Armijo backtracking, step initialised
  *               from the previous accepted step.
+ * A line search takes at most 10 trials (the cubic interpolation shrinks the
+ * step 2-10-fold per trial); a problem whose step shrank 10^8-fold, or that
+ * used its 10 trials without an accepted point, stops unconverged.
  * Every objective is one contraction pass and every H v one dual-number pass
  * (tk_contract with r = m-2).  Writes one report per problem (host array of
  * B entries); returns TK_ENOTCONV if any problem missed tol (a problem also

@@ -93,6 +93,7 @@ def _declare(L):
         "tk_hessian_workspace_size": (sz, [i32, i64]),
         "tk_hessian": (i32, [i32, i64, i32, P, P, P, P, sz, P]),
         "tk_fma_probe": (i32, [i32, i32, ctypes.c_longlong, P, P]),
+        "tk_umma_probe": (i32, [i32, i32, i32, P, P, P, P, sz, P]),
         "tk_primal": (i32, [i32, i64, i64, P, i64, P, P, P]),
         "tk_predict": (i32, [i64, i64, P, i64, P, P, P]),
         "tk_nystrom_select": (i32, [i64, i64, u64, P]),
@@ -233,15 +234,16 @@ def tk_contract_get_config(m: int, n: int, storage="f32", dual: bool = False) ->
 
 class tk_batched_config(ctypes.Structure):
     _fields_ = [("vpl", ctypes.c_int), ("block_bytes", ctypes.c_int), ("nbuf", ctypes.c_int),
-                ("slice_mult", ctypes.c_int), ("min_batch", ctypes.c_int)]
+                ("slice_mult", ctypes.c_int), ("min_batch", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
 
 
-def tk_batched_set_config(vpl=0, block_bytes=0, nbuf=0, slice_mult=0, min_batch=0, reset=False):
-    """Process-wide launch configuration of the batched contraction (0 = library choice)."""
+def tk_batched_set_config(vpl=0, block_bytes=0, nbuf=0, slice_mult=0, min_batch=0, tensor_cores=0, reset=False):
+    """Process-wide launch configuration of the batched contraction (0 = library choice;
+    tensor_cores: 1 = the tcgen05 pass wherever it covers the call, -1 = never)."""
     if reset:
         _check(lib().tk_batched_set_config(None))
         return
-    c = tk_batched_config(vpl, block_bytes, nbuf, slice_mult, min_batch)
+    c = tk_batched_config(vpl, block_bytes, nbuf, slice_mult, min_batch, tensor_cores)
     _check(lib().tk_batched_set_config(ctypes.byref(c)))
 
 
@@ -277,6 +279,23 @@ def tk_fma_probe(dtype="f32", blocks: int = 0, iters: int = 1 << 16, reps: int =
         e1.synchronize()
         best = min(best, e0.elapsed_time(e1) * 1e-3)
     return 2.0 * 16 * iters * 256 * blocks / best
+
+
+def tk_umma_probe(A: torch.Tensor, B: torch.Tensor, split: bool = False, stream=None) -> torch.Tensor:
+    """D = A B^T for one 128 x N tile on the tensor cores (tcgen05.mma,
+    kind::tf32; split=True: the 3-term TF32 split).  A: 128 x k, B: N x k FP32."""
+    assert A.is_cuda and B.is_cuda and A.dtype == torch.float32 and B.dtype == torch.float32
+    A, B = A.contiguous(), B.contiguous()
+    k = A.shape[1]
+    assert A.shape[0] == 128 and B.shape[1] == k
+    D = torch.empty(128, B.shape[0], dtype=torch.float32, device=A.device)
+    work = new_workspace(256, A.device)
+    _check(lib().tk_umma_probe(B.shape[0], k, int(bool(split)), _p(A), _p(B), _p(D), _p(work), work.numel(),
+                               _stream(stream)))
+    rc = tk_status_read(work, stream)
+    if rc != TK_OK:
+        raise TKError(rc, "the tensor-core probe's wait on its MMAs ran out")
+    return D
 
 
 def tk_status_read(work: torch.Tensor, stream=None) -> int:

@@ -38,6 +38,7 @@ def _sources():
 def _digest() -> str:
     h = hashlib.sha256()
     for p in _sources() + sorted(glob.glob(os.path.join(CSRC, "*.h"))) + \
+            sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + \
             [os.path.join(ROOT, "include", "tk.h")]:
         with open(p, "rb") as f:
             h.update(p.encode() + f.read())

@@ -134,6 +134,8 @@ size_t tk_contract_workspace_size(int m, int64_t n, int64_t B) {
   if (dev_info(&di) != TK_OK) return 0;
   size_t need = contract_workspace_bytes((int)n, di.sms);
   if (B > 1) need = std::max(need, batched_workspace_bytes((int)n, B, di.sms));
+  // room for the tensor-core pass wherever the configuration may take it
+  if (tc_covers(m, (int)n, TK_F32, false, B, 0, multiset(n, m))) need = std::max(need, tc_workspace_bytes(m, (int)n, B, di.sms));
   return need;
 }
 
@@ -171,6 +173,7 @@ static int contract_impl(int m, int64_t n, int storage, const void *K, int64_t o
   // kernel wins from B = 28 for K[a^{m-1}] and from B = 16 for the HVP).
   if (B >= batched_min_batch(r == m - 2) && storage != TK_F64) {
     BatchedArgs ba;
+    memset(&ba, 0, sizeof(ba));
     ba.m = m;
     ba.n = (int)n;
     ba.storage = storage;
@@ -185,6 +188,10 @@ static int contract_impl(int m, int64_t n, int storage, const void *K, int64_t o
     ba.S = (r == m - 1) ? S : nullptr;
     ba.work = work;
     ba.work_bytes = work_bytes;
+    if (tc_covers(m, (int)n, storage, r == m - 2, B, off_lo, off_hi)) {
+      rc = contract_batched_tc(ba, st);
+      if (rc != TK_EUNSUPPORTED) return rc;
+    }
     rc = contract_batched(ba, st);
     if (rc != TK_EUNSUPPORTED) return rc;
   }
@@ -269,13 +276,13 @@ int tk_contract_get_config(int m, int64_t n, int storage, int dual, tk_contract_
 
 int tk_batched_set_config(const tk_batched_config *cfg) {
   if (!cfg) {
-    g_batched_cfg = tk_batched_config{0, 0, 0, 0, 0};
+    g_batched_cfg = tk_batched_config{0, 0, 0, 0, 0, 0};
     return TK_OK;
   }
   if (cfg->vpl < 0 || cfg->vpl > 2 ||
       (cfg->block_bytes != 0 && (cfg->block_bytes < 4096 || cfg->block_bytes > 65536 || cfg->block_bytes % 128)) ||
       (cfg->nbuf != 0 && (cfg->nbuf < 2 || cfg->nbuf > 4)) || cfg->slice_mult < 0 || cfg->slice_mult > 2 ||
-      cfg->min_batch < 0)
+      cfg->min_batch < 0 || cfg->tensor_cores < -1 || cfg->tensor_cores > 1)
     return fail(TK_EINVAL, "batched config out of range");
   g_batched_cfg = *cfg;
   return TK_OK;
@@ -291,6 +298,7 @@ int tk_batched_get_config(int m, int64_t n, int storage, int dual, int64_t B, tk
   rc = dev_info(&di);
   if (rc != TK_OK) return rc;
   batched_resolve((int)n, storage, dual != 0, B, di.sms, di.smem_optin, out);
+  out->tensor_cores = tc_covers(m, (int)n, storage, dual != 0, B, 0, multiset(n, m)) ? 1 : 0;
   return TK_OK;
 }
 
@@ -317,6 +325,8 @@ int tk_status_read(void *work, void *stream) {
 int tk_workspace_release(void *work) {
   if (!work) return fail(TK_EINVAL, "NULL workspace");
   forget_plan(work);
+  forget_hessian_plan(work);
+  forget_tc_plan(work);
   return TK_OK;
 }
 

@@ -596,7 +596,7 @@ size_t batched_workspace_bytes(int n, int64_t B, int sms) {
   return sizeof(WsHeader) + batched_plan_bytes(sms) + (size_t)blocks * 2 * (n + 2) * 64 * sizeof(double);
 }
 
-tk_batched_config g_batched_cfg = {0, 0, 0, 0, 0};
+tk_batched_config g_batched_cfg = {0, 0, 0, 0, 0, 0};
 
 int64_t batched_min_batch(bool dual) {
   return g_batched_cfg.min_batch > 0 ? g_batched_cfg.min_batch : (dual ? 16 : 28);
@@ -612,7 +612,7 @@ static size_t batched_smem(int n, bool dual, int vpl, int nbuf, int buf_bytes) {
 
 bool batched_resolve(int n, int storage, bool dual, int64_t B, int sms, int smem_optin, tk_batched_config *out) {
   const tk_batched_config &o = g_batched_cfg;
-  *out = tk_batched_config{0, 0, 0, 0, (int)batched_min_batch(dual)};
+  *out = tk_batched_config{0, 0, 0, 0, (int)batched_min_batch(dual), 0};
   if (storage == TK_F64) return false;
   int vpl = 0, ncol = 0;
   if (!batched_shape(n, dual, &vpl, &ncol)) return false;

@@ -152,9 +152,16 @@ static int ensure_plan(const PlanKey &key, void *work, cudaStream_t st) {
   int dev = 0;
   TK_CUDA_CHECK(cudaGetDevice(&dev));
   void *plan_region = reinterpret_cast<unsigned char *>(work) + sizeof(WsHeader);
+  {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto up = g_uploaded.find({dev, plan_region});
+    if (up != g_uploaded.end() && up->second == key) return TK_OK;
+  }
+  // this upload overwrites what the Hessian and tensor-core passes may have
+  // recorded for the same workspace
+  forget_hessian_plan(work);
+  forget_tc_plan(work);
   std::lock_guard<std::mutex> lk(g_plan_mu);
-  auto up = g_uploaded.find({dev, plan_region});
-  if (up != g_uploaded.end() && up->second == key) return TK_OK;
   auto it = g_plans.find(key);
   if (it == g_plans.end()) {
     if (g_plans.size() > 32) g_plans.clear();

@@ -22,18 +22,24 @@
 // 1/(kb+1) (c = b < d) or 1/((kb+1)(kb+2)) (c = d = b).
 //
 // GB300 mapping.  The output is cut into 32 x 32 tiles of the upper triangle
-// (rows c, columns d >= c).  A work item is one tile and a range of triangles
-// in layout order, cut on the host so that items hold near-equal numbers of
-// entries; one block of 8 warps runs an item.  Warp w owns rows c0+w+8i
-// (i < 4) and lane j column d0+j: for each triangle every thread loads its
-// four entries (row segments of the packed triangle: coalesced), adds term A
-// into registers, and forms the row and column parts of v_Q and of tau_Q.  The
-// row parts are reduced across lanes, the column parts across warps through
-// shared memory; term B is then accumulated per prefix value q into a
+// (rows c, columns d >= c).  The triangles that reach a tile (last prefix
+// value b <= the tile's last row) are listed on the host once per (m, n) --
+// a table of every triangle's packed offset, prefix and multiplicities, and
+// per work item a list of triangle indices -- and a work item is one tile and
+// a run of its list, cut so that items hold near-equal numbers of entries.
+// One block of 8 warps runs an item, 8 triangles at a time: 8 threads fetch
+// the batch's records and form its prefix products; every thread issues its
+// 32 loads (warp w owns rows c0+w+8i, i < 4, lane j column d0+j: row segments
+// of the packed triangles, coalesced), adds term A into registers and forms
+// the row and column parts of v_Q and tau_Q; the warp's 32 row sums are
+// reduced by one butterfly reduce-scatter, the column parts across warps
+// through shared memory.  Term B is accumulated per prefix value q into a
 // shared-memory table Z[q][j] (q <= the tile's last row, j the tile's 64 row
-// and column indices), term C into the FP64 matrix C with atomic adds.  Items
-// write their term-A tile and Z table to their own slots; a second kernel sums
-// the slots in a fixed order and adds C.  Every entry is read from HBM once.
+// and column indices) by 64 threads, each owning one column j and taking the
+// batch's triangles in order; term C goes into the FP64 matrix C with atomic
+// adds.  Items write their term-A tile and Z table to their own slots; a
+// second kernel sums the slots in a fixed order and adds C.  Every entry is
+// read from HBM once.
 #include <cuda_bf16.h>
 #include <stddef.h>
 #include <string.h>
@@ -50,26 +56,37 @@ namespace tk {
 constexpr int kHT = 32;       // tile rows and columns
 constexpr int kHW = 8;        // warps per block
 constexpr int kHFlush = 64;   // triangles between flushes of the term-A registers (FP32 storage)
+constexpr int kHB = 8;        // triangles per batch (one barrier pair per batch)
 constexpr int kHMaxZBytes = 200 * 1024;
 
-// One work item: tile (ti, tj) and the triangles whose (m-2)-tuple rank lies
-// in [q_lo, q_hi); Q is the first of them, base the packed offset of (Q, b, b).
+// One work item: tile (ti, tj) and the triangles pairs[pair_lo, pair_hi) of
+// the triangle table (all of them reach the tile).
 struct HItem {
   int ti, tj;
   int zrows;      // rows of the Z table (prefix values 0 .. zrows-1)
   int pad;
-  int64_t q_lo, q_hi;
-  int64_t base;
+  int64_t pair_lo, pair_hi;
   int64_t zoff;   // offset of the item's Z slot (in values)
-  int32_t Q[kMaxOrder];
 };
-static_assert(sizeof(HItem) == 80, "hessian item");
+static_assert(sizeof(HItem) == 40, "hessian item");
+
+// One triangle: its packed offset (of (Q, b, b)), prefix values, last prefix
+// value b, its multiplicity kb = cnt_Q(b) and M' = m!/prod_v cnt_Q(v)!.
+struct HTriRec {
+  int64_t base;
+  uint16_t Q[kMaxOrder];
+  int32_t b, kb;
+  int32_t mprime, pad;
+};
+static_assert(sizeof(HTriRec) == 40, "triangle record");
 
 struct HParams {
   int m, n;
   const unsigned char *K;
   const double *alpha;
   const HItem *items;
+  const HTriRec *tris;
+  const int32_t *pairs;
   int nitems;
   int nt;              // tiles per side
   double *Apart;       // [item][32][32]
@@ -78,33 +95,6 @@ struct HParams {
   int *status;
   int pieces;          // plan key: number of items
 };
-
-// First triangle at or after Q (lexicographic over sorted (m-2)-tuples) whose
-// last value b is <= cmax: the prefix before the first position holding a
-// value above cmax is advanced.  Returns false when none is left.
-__host__ __device__ inline bool skip_to_useful(int m, int n, int cmax, int32_t *Q) {
-  if (m <= 2) return true;
-  const int len = m - 2;
-  for (;;) {
-    int j = 0;
-    while (j < len && Q[j] <= cmax) ++j;
-    if (j == len) return true;
-    if (j == 0) return false;
-    if (!next_sorted(j, n, Q)) return false;
-    for (int i = j; i < len; ++i) Q[i] = Q[j - 1];
-  }
-}
-
-// offset of (Q, b, b): the rank of the (m)-tuple Q b b
-__host__ __device__ inline int64_t tri_base(int m, int n, const int32_t *Q) {
-  if (m <= 2) return 0;
-  int32_t t[kMaxOrder];
-  for (int j = 0; j < m - 2; ++j) t[j] = Q[j];
-  t[m - 2] = t[m - 1] = Q[m - 3];
-  return rank(m, n, t);
-}
-
-__host__ __device__ inline int64_t qrank(int m, int n, const int32_t *Q) { return m <= 2 ? 0 : rank(m - 2, n, Q); }
 
 template <typename ST, typename CT>
 __device__ __forceinline__ CT ld_k(const unsigned char *K, int64_t off) {
@@ -115,6 +105,45 @@ __device__ __forceinline__ double ld_k<float, double>(const unsigned char *K, in
   return (double)reinterpret_cast<const float *>(K)[off];
 }
 
+// Per-triangle constants of a batch in shared memory: the prefix and, for
+// term B, the distinct prefix values q with their coefficients cnt_q B_q.
+template <typename CT>
+struct HTri {
+  int32_t Q[kMaxOrder];
+  int nq;
+  int qv[kMaxOrder];
+  CT qc[kMaxOrder];
+};
+
+// Per (triangle, tile row) constants: the offset of the row's entry at column
+// 0 (base + row offset - c; -1 when the row is not in the triangle), the
+// entry weight w, the term-A weight A_Q w, and the extra factor of the head
+// entry d = c.
+template <typename CT>
+struct HRow {
+  int64_t base;
+  CT cw, ca, dg;
+};
+
+// Sum of the 32 values v[0..31] held by every lane over the warp's lanes,
+// scattered so that lane l ends with the sum of v[l]: five halving exchange
+// steps (16 + 8 + 4 + 2 + 1 shuffles).
+template <typename CT>
+__device__ __forceinline__ CT warp_reduce_scatter32(CT (&v)[32], int lane) {
+#pragma unroll
+  for (int k = 16; k >= 1; k >>= 1) {
+    const bool up = (lane & k) != 0;
+#pragma unroll
+    for (int j = 0; j < k; ++j) {
+      // keep the half of the pair this lane is responsible for, send the other
+      const CT send = up ? v[j] : v[j + k];
+      const CT keep = up ? v[j + k] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, k);
+    }
+  }
+  return v[0];
+}
+
 template <typename ST, typename CT>
 __global__ void __launch_bounds__(kHW * 32) hess_kernel(HParams p) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -123,162 +152,186 @@ __global__ void __launch_bounds__(kHW * 32) hess_kernel(HParams p) {
   if (plan_is_stale(p.status, m, n, p.pieces, -1, -1)) return;
   const HItem it = p.items[blockIdx.x];
   const int c0 = kHT * it.ti, d0 = kHT * it.tj;
-  const int cmax = min(c0 + kHT, n) - 1;
   const bool diag = it.ti == it.tj;
-  CT *a_s = reinterpret_cast<CT *>(smem);                        // [n]
-  CT *Z = a_s + ((n + 1) & ~1);                                  // [zrows][64]
-  CT *rowbuf = Z + (size_t)it.zrows * 64;                        // [2][32]
-  CT *colbuf = rowbuf + 2 * 32;                                  // [2][8][32]
-  CT *taubuf = colbuf + 2 * kHW * 32;                            // [2][8]
+  CT *a_s = reinterpret_cast<CT *>(smem);                       // [n]
+  CT *Z = a_s + ((n + 1) & ~1);                                 // [zrows][64]
+  CT *rowbuf = Z + (size_t)it.zrows * 64;                       // [kHB][32]
+  CT *colbuf = rowbuf + kHB * 32;                               // [kHB][8][32]
+  CT *taubuf = colbuf + kHB * kHW * 32;                         // [kHB][8]
+  HTri<CT> *tri = reinterpret_cast<HTri<CT> *>(taubuf + kHB * kHW);  // [kHB]
+  HRow<CT> *rows = reinterpret_cast<HRow<CT> *>(tri + kHB);          // [kHB][32]
   for (int i = threadIdx.x; i < n; i += blockDim.x) a_s[i] = (CT)p.alpha[i];
   for (int i = threadIdx.x; i < it.zrows * 64; i += blockDim.x) Z[i] = CT(0);
-  __syncthreads();
 
   const int d = d0 + lane;
-  const CT ad = d < n ? a_s[d] : CT(0);
   int crow[4];
-  CT arow[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    crow[i] = c0 + w + 8 * i;
-    arow[i] = crow[i] < n ? a_s[crow[i]] : CT(0);
-  }
+  for (int i = 0; i < 4; ++i) crow[i] = c0 + w + 8 * i;
   CT accA[4] = {CT(0), CT(0), CT(0), CT(0)};
   double accA64[4] = {0.0, 0.0, 0.0, 0.0};
   const CT inv_mm1 = CT(1) / CT(m * (m - 1));
+  int since_flush = 0;
+  __syncthreads();
+  const CT ad = d < n ? a_s[d] : CT(0);
+  CT arow[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) arow[i] = crow[i] < n ? a_s[crow[i]] : CT(0);
 
-  int32_t Q[kMaxOrder];
-  for (int j = 0; j < kMaxOrder; ++j) Q[j] = it.Q[j];
-  int64_t qr = it.q_lo;
-  int64_t base = it.base;
-  int parity = 0, since_flush = 0;
-  while (qr < it.q_hi) {
-    const int b = (m > 2) ? Q[m - 3] : -1;
-    if (b > cmax) {
-      if (!skip_to_useful(m, n, cmax, Q)) break;
-      qr = qrank(m, n, Q);
-      base = tri_base(m, n, Q);
-      continue;
+  for (int64_t pos = it.pair_lo; pos < it.pair_hi; pos += kHB) {
+    const int nb = (int)(it.pair_hi - pos < kHB ? it.pair_hi - pos : kHB);
+    // ---- the batch's constants: thread (q, r) takes triangle q, tile row r
+    {
+      const int q = threadIdx.x >> 5, r = threadIdx.x & 31;
+      if (q < nb) {
+        const HTriRec rec = p.tris[p.pairs[pos + q]];
+        CT AQ = CT(1);
+        for (int j = 0; j < m - 2; ++j) AQ *= a_s[rec.Q[j]];
+        const int b = rec.b, bb = b < 0 ? 0 : b;
+        const int c = c0 + r;
+        const bool in = c >= bb && c < n;
+        const bool first = c == b;
+        HRow<CT> hr;
+        hr.base = in ? rec.base + (int64_t)(c - bb) * (2 * n - bb - c + 1) / 2 - c : -1;
+        hr.cw = CT(rec.mprime) * inv_mm1 * (first ? kInvSmall<CT>[rec.kb + 1] : CT(1));
+        hr.ca = AQ * hr.cw;
+        hr.dg = first ? kInvSmall<CT>[rec.kb + 2] : CT(0.5);
+        rows[q * 32 + r] = hr;
+        if (r == 0) {
+          // term B: the distinct prefix values and cnt_q B_q (B_q = A_Q without one factor of q)
+          HTri<CT> &t = tri[q];
+          int nq = 0;
+          for (int j = 0; j < m - 2; ++j) {
+            t.Q[j] = rec.Q[j];
+            if (j > 0 && rec.Q[j] == rec.Q[j - 1]) continue;
+            const int qv = rec.Q[j];
+            int cnt = 0;
+            CT Bq = CT(1);
+            bool skipped = false;
+            for (int jj = 0; jj < m - 2; ++jj) {
+              if (rec.Q[jj] == qv) {
+                ++cnt;
+                if (!skipped) {
+                  skipped = true;
+                  continue;
+                }
+              }
+              Bq *= a_s[rec.Q[jj]];
+            }
+            t.qv[nq] = qv;
+            t.qc[nq] = CT(cnt) * Bq;
+            ++nq;
+          }
+          t.nq = nq;
+        }
+      }
     }
-    // triangle constants (uniform over the block)
-    uint64_t mp = 1;
-    for (int i = 2; i <= m; ++i) mp *= (uint64_t)i;
-    CT AQ = CT(1);
-    int run = 0;
-    for (int j = 0; j < m - 2; ++j) {
-      AQ *= a_s[Q[j]];
-      run = (j > 0 && Q[j] == Q[j - 1]) ? run + 1 : 1;
-      if (run > 1) mp = exact_div_small(mp, run);
-    }
-    const int kb = (m > 2) ? run : 0;
-    const CT w0 = CT(mp) * inv_mm1;
-    const CT f_first = CT(1) / CT(kb + 1), f_firstdiag = CT(1) / CT(kb + 2);
-    const int bb = b < 0 ? 0 : b;
-    const int L = n - bb;
-
-    // the four entries of this thread (rows c >= b, columns d >= c)
-    CT x[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int c = crow[i];
-      const bool ok = c >= bb && c < n && d >= c && d < n;
-      const int64_t ro = (int64_t)(c - bb) * (2 * n - bb - c + 1) / 2;
-      x[i] = ok ? ld_k<ST, CT>(p.K, base + ro + (d - c)) : CT(0);
-    }
-    CT rowp[4], colp = CT(0);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int c = crow[i];
-      const bool first = c == b, dg = d == c;
-      const CT f = (first ? f_first : CT(1)) * (dg ? (first ? f_firstdiag : CT(0.5)) : CT(1));
-      const CT wx = w0 * f * x[i];
-      accA[i] += AQ * (dg ? CT(2) * wx : wx);
-      rowp[i] = wx * ad;
-      colp += wx * arow[i];
-    }
-    CT tau_w = CT(0);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      CT r = rowp[i];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-      rowp[i] = r;
-      tau_w += arow[i] * r;
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) rowbuf[parity * 32 + w + 8 * i] = rowp[i];
-      taubuf[parity * kHW + w] = tau_w;
-    }
-    colbuf[(parity * kHW + w) * 32 + lane] = colp;
     __syncthreads();
-    // term B: Z[q][slot] += cnt_q B_q v_Q[slot] for each distinct q of Q
+
+    // ---- loads of every triangle of the batch first, then the sums
+    CT x[kHB][4];
+#pragma unroll
+    for (int q = 0; q < kHB; ++q) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        x[q][i] = CT(0);
+        if (q < nb) {
+          const int64_t rb = rows[q * 32 + w + 8 * i].base;
+          if (rb >= 0 && d >= crow[i] && d < n) x[q][i] = ld_k<ST, CT>(p.K, rb + d);
+        }
+      }
+    }
+    CT rv[32];
+    CT colp[kHB];
+#pragma unroll
+    for (int q = 0; q < kHB; ++q) {
+      colp[q] = CT(0);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const HRow<CT> &hr = rows[q * 32 + w + 8 * i];
+        const bool dgl = d == crow[i];
+        // slots past the batch's last triangle and rows outside a triangle
+        // hold x = 0; their constants are never used unguarded
+        const CT xe = (q < nb) ? x[q][i] : CT(0);
+        const CT cw = (q < nb) ? hr.cw : CT(0), ca = (q < nb) ? hr.ca : CT(0);
+        const CT f = dgl ? ((q < nb) ? hr.dg : CT(0)) : CT(1);
+        const CT wx = cw * f * xe;
+        accA[i] += ca * (dgl ? CT(2) * f : f) * xe;
+        rv[q * 4 + i] = wx * ad;
+        colp[q] += wx * arow[i];
+      }
+    }
+    // lane l: the row part of row c0 + w + 8 (l & 3) for triangle l >> 2
+    const CT rsum = warp_reduce_scatter32(rv, lane);
+    {
+      const int q = lane >> 2, i = lane & 3;
+      CT tv = arow[0];
+#pragma unroll
+      for (int k = 1; k < 4; ++k) tv = (i == k) ? arow[k] : tv;
+      tv *= rsum;
+      tv += __shfl_xor_sync(0xffffffffu, tv, 1);
+      tv += __shfl_xor_sync(0xffffffffu, tv, 2);
+      rowbuf[q * 32 + w + 8 * i] = rsum;
+      if (i == 0) taubuf[q * kHW + w] = tv;
+    }
+#pragma unroll
+    for (int q = 0; q < kHB; ++q) colbuf[(q * kHW + w) * 32 + lane] = colp[q];
+    __syncthreads();
+
+    // ---- term B: thread t < 64 owns column slot t of the Z table and adds
+    // the batch's triangles in order
     if (m > 2 && threadIdx.x < 64 && (!diag || threadIdx.x < 32)) {
       const int t = threadIdx.x;
-      CT v;
-      if (t < 32) {
-        v = rowbuf[parity * 32 + t];
-        if (diag)
-          for (int ww = 0; ww < kHW; ++ww) v += colbuf[(parity * kHW + ww) * 32 + t];
-      } else {
-        v = CT(0);
-        for (int ww = 0; ww < kHW; ++ww) v += colbuf[(parity * kHW + ww) * 32 + t - 32];
-      }
-      for (int j = 0; j < m - 2; ++j) {
-        if (j > 0 && Q[j] == Q[j - 1]) continue;
-        const int q = Q[j];
-        int cnt = 0;
-        CT Bq = CT(1);
-        bool skipped = false;
-        for (int jj = 0; jj < m - 2; ++jj) {
-          if (Q[jj] == q) {
-            ++cnt;
-            if (!skipped) {
-              skipped = true;
-              continue;
-            }
-          }
-          Bq *= a_s[Q[jj]];
+      for (int q = 0; q < nb; ++q) {
+        CT v;
+        if (t < 32) {
+          v = rowbuf[q * 32 + t];
+          if (diag)
+            for (int ww = 0; ww < kHW; ++ww) v += colbuf[(q * kHW + ww) * 32 + t];
+        } else {
+          v = CT(0);
+          for (int ww = 0; ww < kHW; ++ww) v += colbuf[(q * kHW + ww) * 32 + t - 32];
         }
-        Z[(size_t)q * 64 + t] += CT(cnt) * Bq * v;
+        const HTri<CT> &tq = tri[q];
+        for (int j = 0; j < tq.nq; ++j) Z[(size_t)tq.qv[j] * 64 + t] += tq.qc[j] * v;
       }
     }
-    // term C: Hk[q][q'] += (ordered pairs of Q positions holding q, q') B tau
-    if (m > 3 && threadIdx.x == 64) {
+    // ---- term C: one thread per triangle (warp 2)
+    if (m > 3 && threadIdx.x >= 64 && threadIdx.x < 64 + nb) {
+      const int q = threadIdx.x - 64;
+      const int32_t *Qq = tri[q].Q;
       CT tau = CT(0);
-      for (int ww = 0; ww < kHW; ++ww) tau += taubuf[parity * kHW + ww];
+      for (int ww = 0; ww < kHW; ++ww) tau += taubuf[q * kHW + ww];
       for (int j = 0; j < m - 2; ++j) {
-        if (j > 0 && Q[j] == Q[j - 1]) continue;
+        if (j > 0 && Qq[j] == Qq[j - 1]) continue;
         for (int k = 0; k < m - 2; ++k) {
-          if (k > 0 && Q[k] == Q[k - 1]) continue;
-          const int q = Q[j], q2 = Q[k];
-          int cq = 0, cq2 = 0;
+          if (k > 0 && Qq[k] == Qq[k - 1]) continue;
+          const int qa = Qq[j], qb = Qq[k];
+          int ca = 0, cb = 0;
           for (int jj = 0; jj < m - 2; ++jj) {
-            cq += Q[jj] == q;
-            cq2 += Q[jj] == q2;
+            ca += Qq[jj] == qa;
+            cb += Qq[jj] == qb;
           }
-          const int pairs = (q == q2) ? cq * (cq - 1) : cq * cq2;
+          const int pairs = (qa == qb) ? ca * (ca - 1) : ca * cb;
           if (pairs == 0) continue;
-          // B without one copy of q and one of q2
           CT Bqq = CT(1);
-          int skip_q = 1, skip_q2 = 1;
+          int skip_a = 1, skip_b = 1;
           for (int jj = 0; jj < m - 2; ++jj) {
-            if (Q[jj] == q && skip_q) {
-              skip_q = 0;
+            if (Qq[jj] == qa && skip_a) {
+              skip_a = 0;
               continue;
             }
-            if (Q[jj] == q2 && skip_q2) {
-              skip_q2 = 0;
+            if (Qq[jj] == qb && skip_b) {
+              skip_b = 0;
               continue;
             }
-            Bqq *= a_s[Q[jj]];
+            Bqq *= a_s[Qq[jj]];
           }
-          atomicAdd(&p.C[(size_t)q * n + q2], (double)(CT(pairs) * Bqq * tau));
+          atomicAdd(&p.C[(size_t)qa * n + qb], (double)(CT(pairs) * Bqq * tau));
         }
       }
     }
-    parity ^= 1;
-    if (sizeof(CT) == 4 && ++since_flush == kHFlush) {
+    since_flush += nb;
+    if (sizeof(CT) == 4 && since_flush >= kHFlush) {
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         accA64[i] += (double)accA[i];
@@ -286,11 +339,8 @@ __global__ void __launch_bounds__(kHW * 32) hess_kernel(HParams p) {
       }
       since_flush = 0;
     }
-    base += (int64_t)L * (L + 1) / 2;
-    if (m <= 2 || !next_sorted(m - 2, n, Q)) break;
-    ++qr;
+    __syncthreads();  // the batch's tables are read; the next batch may overwrite them
   }
-  __syncthreads();
   // the item's slots: term-A tile and Z table
   double *A = p.Apart + (size_t)blockIdx.x * kHT * kHT;
 #pragma unroll
@@ -303,10 +353,16 @@ __global__ void __launch_bounds__(kHW * 32) hess_kernel(HParams p) {
 // (min(r,s), max(r,s)), term B of every item whose tile has r or s among its
 // row or column indices, and term C.
 __global__ void hess_assemble(int m, int n, int nt, const HItem *items, const int *item_of_tile,
-                              const double *Apart, const double *Zpart, const double *C, double *H) {
+                              const double *Apart, const double *Zpart, const double *C, double *H,
+                              const int *status, int nitems) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   if (s >= n) return;
+  // the plan the items come from must be this launch's (see hess_kernel):
+  // on a mismatch write nothing and read no item
+  const volatile WsHeader *wh = reinterpret_cast<const volatile WsHeader *>(status);
+  if (!(wh->plan_m == m && wh->plan_n == n && wh->plan_pieces == nitems && wh->plan_lo == -1 && wh->plan_hi == -1))
+    return;
   const int lo = min(r, s), hi = max(r, s);
   double h = 0.0;
   {  // term A
@@ -344,98 +400,96 @@ __global__ void hess_assemble(int m, int n, int nt, const HItem *items, const in
 struct HPlan {
   std::vector<HItem> items;
   std::vector<int> item_of_tile;  // tiles + 1 prefix
+  std::vector<HTriRec> tris;      // every triangle, layout order
+  std::vector<int32_t> pairs;     // per item, the triangles it takes
   int64_t zvalues;
   int zrows_max;
 };
 
 static void build_hplan(int m, int n, int target_items, HPlan *out) {
   const int nt = (n + kHT - 1) / kHT;
+  // every triangle in layout order, with its offset and multiplicities; the
+  // triangles of each last prefix value b in a list of their own
+  out->tris.clear();
+  std::vector<std::vector<int32_t>> by_b(n + 1);  // index b + 1 (m = 2: b = -1)
+  {
+    int32_t Q[kMaxOrder] = {0};
+    int64_t base = 0;
+    uint64_t mfact = 1;
+    for (int i = 2; i <= m; ++i) mfact *= (uint64_t)i;
+    for (;;) {
+      HTriRec r;
+      memset(&r, 0, sizeof(r));
+      r.base = base;
+      for (int j = 0; j < kMaxOrder; ++j) r.Q[j] = (uint16_t)Q[j];
+      uint64_t mp = mfact;
+      int run = 0;
+      for (int j = 0; j < m - 2; ++j) {
+        run = (j > 0 && Q[j] == Q[j - 1]) ? run + 1 : 1;
+        if (run > 1) mp = exact_div_small(mp, run);
+      }
+      r.b = (m > 2) ? Q[m - 3] : -1;
+      r.kb = (m > 2) ? run : 0;
+      r.mprime = (int32_t)mp;
+      by_b[r.b + 1].push_back((int32_t)out->tris.size());
+      out->tris.push_back(r);
+      const int L = n - (r.b < 0 ? 0 : r.b);
+      base += (int64_t)L * (L + 1) / 2;
+      if (m <= 2 || !next_sorted(m - 2, n, Q)) break;
+    }
+  }
   std::vector<std::pair<int, int>> tiles;
   for (int ti = 0; ti < nt; ++ti)
     for (int tj = ti; tj < nt; ++tj) tiles.push_back({ti, tj});
   // cost of a triangle with last value b in a tile: its entries there plus a
-  // fixed per-triangle overhead of the loop
+  // fixed per-triangle overhead
   const int64_t kTriCost = 256;
-  auto tile_cost = [&](int ti, int tj, std::vector<int64_t> &cost_b) {
-    const int c0 = kHT * ti, c1 = std::min(c0 + kHT, n) - 1, d0 = kHT * tj, d1 = std::min(d0 + kHT, n) - 1;
-    cost_b.assign(n + 1, 0);
-    for (int b = -1; b < n; ++b) {
+  std::vector<std::vector<int64_t>> cost(tiles.size(), std::vector<int64_t>(n + 1, 0));
+  int64_t total = 0;
+  for (size_t k = 0; k < tiles.size(); ++k) {
+    const int c0 = kHT * tiles[k].first, c1 = std::min(c0 + kHT, n) - 1;
+    const int d0 = kHT * tiles[k].second, d1 = std::min(d0 + kHT, n) - 1;
+    for (int b = -1; b <= c1 && b < n; ++b) {
       int64_t e = 0;
       for (int c = std::max(std::max(b, 0), c0); c <= c1; ++c) e += std::max(0, d1 - std::max(c, d0) + 1);
-      cost_b[b + 1] = (b <= c1) ? e + kTriCost : 0;
-    }
-  };
-  // total cost
-  std::vector<int64_t> cost_b;
-  int64_t total = 0;
-  const int64_t ntri = (m > 2) ? multiset(n, m - 2) : 1;
-  for (auto &t : tiles) {
-    tile_cost(t.first, t.second, cost_b);
-    if (m <= 2) {
-      total += cost_b[0];
-      continue;
-    }
-    int32_t Q[kMaxOrder] = {0};
-    const int cmax = std::min(kHT * t.first + kHT, n) - 1;
-    for (;;) {
-      if (!skip_to_useful(m, n, cmax, Q)) break;
-      total += cost_b[Q[m - 3] + 1];
-      if (!next_sorted(m - 2, n, Q)) break;
+      cost[k][b + 1] = e + kTriCost;
+      total += cost[k][b + 1] * (int64_t)by_b[b + 1].size();
     }
   }
   const int64_t target = std::max<int64_t>(1, total / std::max(1, target_items));
   out->items.clear();
+  out->pairs.clear();
   out->item_of_tile.assign(tiles.size() + 1, 0);
   int64_t zoff = 0;
   int zmax = 0;
-  for (size_t ti = 0; ti < tiles.size(); ++ti) {
-    out->item_of_tile[ti] = (int)out->items.size();
-    const int tI = tiles[ti].first, tJ = tiles[ti].second;
-    tile_cost(tI, tJ, cost_b);
-    const int cmax = std::min(kHT * tI + kHT, n) - 1;
-    const int zrows = cmax + 1;
-    auto emit = [&](const int32_t *Qs, int64_t qlo, int64_t qhi) {
+  for (size_t k = 0; k < tiles.size(); ++k) {
+    out->item_of_tile[k] = (int)out->items.size();
+    const int cmax = std::min(kHT * tiles[k].first + kHT, n) - 1;
+    const int zrows = (m > 2) ? cmax + 1 : 0;
+    int64_t lo = (int64_t)out->pairs.size(), acc = 0;
+    auto emit = [&]() {
       HItem h;
       memset(&h, 0, sizeof(h));
-      h.ti = tI;
-      h.tj = tJ;
-      h.zrows = (m > 2) ? zrows : 0;
-      h.q_lo = qlo;
-      h.q_hi = qhi;
-      for (int j = 0; j < kMaxOrder; ++j) h.Q[j] = Qs[j];
-      h.base = tri_base(m, n, Qs);
+      h.ti = tiles[k].first;
+      h.tj = tiles[k].second;
+      h.zrows = zrows;
+      h.pair_lo = lo;
+      h.pair_hi = (int64_t)out->pairs.size();
       h.zoff = zoff;
-      zoff += (int64_t)h.zrows * 64;
-      zmax = std::max(zmax, h.zrows);
+      zoff += (int64_t)zrows * 64;
+      zmax = std::max(zmax, zrows);
       out->items.push_back(h);
+      lo = h.pair_hi;
+      acc = 0;
     };
-    int32_t Q[kMaxOrder] = {0};
-    if (m <= 2) {
-      emit(Q, 0, 1);
-      continue;
-    }
-    if (!skip_to_useful(m, n, cmax, Q)) continue;
-    int32_t Qs[kMaxOrder];
-    memcpy(Qs, Q, sizeof(Qs));
-    int64_t qs = qrank(m, n, Q), acc = 0;
-    for (;;) {
-      acc += cost_b[Q[m - 3] + 1];
-      int32_t Qn[kMaxOrder];
-      memcpy(Qn, Q, sizeof(Qn));
-      const bool more = next_sorted(m - 2, n, Qn) && skip_to_useful(m, n, cmax, Qn);
-      if (!more) {
-        emit(Qs, qs, ntri);
-        break;
+    for (int b = -1; b <= cmax && b < n; ++b) {
+      for (int32_t t : by_b[b + 1]) {
+        out->pairs.push_back(t);
+        acc += cost[k][b + 1];
+        if (acc >= target) emit();
       }
-      if (acc >= target) {
-        const int64_t qn = qrank(m, n, Qn);
-        emit(Qs, qs, qn);
-        memcpy(Qs, Qn, sizeof(Qs));
-        qs = qn;
-        acc = 0;
-      }
-      memcpy(Q, Qn, sizeof(Q));
     }
+    if ((int64_t)out->pairs.size() > lo || out->items.size() == (size_t)out->item_of_tile[k]) emit();
   }
   out->item_of_tile[tiles.size()] = (int)out->items.size();
   out->zvalues = zoff;
@@ -452,6 +506,13 @@ static std::map<std::pair<int, const void *>, HKey> g_hup;
 
 static int hess_target(int sms) { return sms * 4; }
 
+void forget_hessian_plan(void *work) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> lk(g_hmu);
+  g_hup.erase({dev, work});
+}
+
 static const HPlan &hplan_for(int m, int n, int sms) {
   HKey k{m, n, hess_target(sms)};
   auto it = g_hplans.find(k);
@@ -464,9 +525,9 @@ static const HPlan &hplan_for(int m, int n, int sms) {
   return it->second;
 }
 
-// workspace: header | items (cap) | item_of_tile (cap) | Apart | Zpart | C
+// workspace: header | items | item_of_tile | triangle table | pairs | Apart | Zpart | C
 struct HLayout {
-  size_t items, iot, apart, zpart, cmat, total;
+  size_t items, iot, tris, pairs, apart, zpart, cmat, total;
 };
 static HLayout hess_layout(int n, const HPlan &pl) {
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
@@ -476,6 +537,10 @@ static HLayout hess_layout(int n, const HPlan &pl) {
   off = al(off + pl.items.size() * sizeof(HItem));
   L.iot = off;
   off = al(off + pl.item_of_tile.size() * sizeof(int));
+  L.tris = off;
+  off = al(off + pl.tris.size() * sizeof(HTriRec));
+  L.pairs = off;
+  off = al(off + pl.pairs.size() * sizeof(int32_t));
   L.apart = off;
   off = al(off + pl.items.size() * kHT * kHT * sizeof(double));
   L.zpart = off;
@@ -507,7 +572,11 @@ extern "C" int tk_hessian(int m, int64_t n, int storage, const void *K, const do
   if (!K || !alpha || !H || !work) return fail(TK_EINVAL, "NULL pointer");
   const int csize = storage == TK_F64 ? 8 : 4;
   const int64_t zrows_cap = (int64_t)n;  // prefix values lie in [0, n)
-  const size_t zbytes = (size_t)zrows_cap * 64 * csize + ((n + 1) & ~1) * csize + (2 * 32 + 2 * kHW * 32 + 2 * kHW) * csize;
+  const size_t tri_bytes = (storage == TK_F64) ? sizeof(HTri<double>) : sizeof(HTri<float>);
+  const size_t row_bytes = (storage == TK_F64) ? sizeof(HRow<double>) : sizeof(HRow<float>);
+  const size_t fixed = ((n + 1) & ~1) * csize + (size_t)(kHB * 32 + kHB * kHW * 32 + kHB * kHW) * csize + 16 +
+                       kHB * tri_bytes + 16 + kHB * 32 * row_bytes;
+  const size_t zbytes = (size_t)zrows_cap * 64 * csize + fixed;
   if (n > TK_MAX_POINTS || zbytes > (size_t)kHMaxZBytes)
     return fail(TK_EUNSUPPORTED, "hessian pass: n=%lld too large for the shared-memory table (%zu bytes)",
                 (long long)n, zbytes);
@@ -520,6 +589,10 @@ extern "C" int tk_hessian(int m, int64_t n, int storage, const void *K, const do
   int dev = 0;
   TK_CUDA_CHECK(cudaGetDevice(&dev));
   unsigned char *ws = reinterpret_cast<unsigned char *>(work);
+  // the Hessian plan occupies the same region of a workspace as the
+  // contraction plans: whatever those recorded for this address is void
+  forget_plan(work);
+  forget_tc_plan(work);
   std::lock_guard<std::mutex> lk(g_hmu);
   const HPlan &pl = hplan_for(m, (int)n, di.sms);
   const HLayout L = hess_layout((int)n, pl);
@@ -531,6 +604,10 @@ extern "C" int tk_hessian(int m, int64_t n, int storage, const void *K, const do
     TK_CUDA_CHECK(cudaMemcpyAsync(ws + L.items, pl.items.data(), pl.items.size() * sizeof(HItem),
                                   cudaMemcpyHostToDevice, st));
     TK_CUDA_CHECK(cudaMemcpyAsync(ws + L.iot, pl.item_of_tile.data(), pl.item_of_tile.size() * sizeof(int),
+                                  cudaMemcpyHostToDevice, st));
+    TK_CUDA_CHECK(cudaMemcpyAsync(ws + L.tris, pl.tris.data(), pl.tris.size() * sizeof(HTriRec),
+                                  cudaMemcpyHostToDevice, st));
+    TK_CUDA_CHECK(cudaMemcpyAsync(ws + L.pairs, pl.pairs.data(), pl.pairs.size() * sizeof(int32_t),
                                   cudaMemcpyHostToDevice, st));
     const WsHeader h = plan_key(m, (int)n, -1, -1, nitems);
     TK_CUDA_CHECK(cudaMemcpyAsync(ws + offsetof(WsHeader, plan_m),
@@ -545,6 +622,8 @@ extern "C" int tk_hessian(int m, int64_t n, int storage, const void *K, const do
   hp.K = reinterpret_cast<const unsigned char *>(K);
   hp.alpha = alpha;
   hp.items = reinterpret_cast<const HItem *>(ws + L.items);
+  hp.tris = reinterpret_cast<const HTriRec *>(ws + L.tris);
+  hp.pairs = reinterpret_cast<const int32_t *>(ws + L.pairs);
   hp.nitems = nitems;
   hp.nt = (int)((n + kHT - 1) / kHT);
   hp.Apart = reinterpret_cast<double *>(ws + L.apart);
@@ -553,8 +632,7 @@ extern "C" int tk_hessian(int m, int64_t n, int storage, const void *K, const do
   hp.status = reinterpret_cast<int *>(ws);
   hp.pieces = nitems;
   TK_CUDA_CHECK(cudaMemsetAsync(hp.C, 0, (size_t)n * n * sizeof(double), st));
-  const size_t smem = (size_t)pl.zrows_max * 64 * csize + ((n + 1) & ~1) * csize +
-                      (2 * 32 + 2 * kHW * 32 + 2 * kHW) * csize;
+  const size_t smem = (size_t)pl.zrows_max * 64 * csize + fixed;
   if (nitems > 0) {
     if (storage == TK_F64) {
       TK_CUDA_CHECK(cudaFuncSetAttribute(hess_kernel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -573,7 +651,7 @@ extern "C" int tk_hessian(int m, int64_t n, int storage, const void *K, const do
   }
   dim3 g((unsigned)((n + 127) / 128), (unsigned)n);
   hess_assemble<<<g, 128, 0, st>>>(m, (int)n, hp.nt, hp.items, reinterpret_cast<const int *>(ws + L.iot), hp.Apart,
-                                   hp.Zpart, hp.C, H);
+                                   hp.Zpart, hp.C, H, hp.status, nitems);
   TK_CUDA_CHECK(cudaGetLastError());
   return TK_OK;
 }

@@ -38,7 +38,8 @@ struct WsHeader {
 static_assert(sizeof(WsHeader) == 256, "header size");
 
 // where-codes of the status word
-enum { kSiteContractWait = 1, kSiteBatchedWait = 3, kSiteStalePlan = 4, kSiteDiagWait = 9 };
+enum { kSiteContractWait = 1, kSiteBatchedWait = 3, kSiteStalePlan = 4, kSiteUmmaWait = 5, kSiteTcWait = 6,
+       kSiteDiagWait = 9 };
 
 // The key to write into a workspace header after its plan region was filled.
 inline WsHeader plan_key(int m, int n, int64_t lo, int64_t hi, int pieces) {
@@ -72,6 +73,10 @@ int plan_to_device(int m, int n, int64_t lo, int64_t hi, int pieces, int row_cos
 // memory is about to hold something else, or is new memory at an address a
 // workspace used before).
 void forget_plan(void *work);
+// The same for the Hessian pass's plan cached for the workspace at `work`.
+void forget_hessian_plan(void *work);
+// The same for the tensor-core batched contraction's plan.
+void forget_tc_plan(void *work);
 
 // Batched contraction (one pass for B vectors); returns TK_EUNSUPPORTED when
 // the shape is outside what the batched kernel covers (callers then loop).
@@ -89,6 +94,12 @@ struct BatchedArgs {
   size_t work_bytes;
 };
 int contract_batched(const BatchedArgs &a, cudaStream_t st);
+// Tensor-core batched contraction (r = m-1, whole tensor, FP32/BF16 storage,
+// n <= 320): whether the current configuration takes it for this call, the
+// workspace it needs, and the pass itself.
+bool tc_covers(int m, int n, int storage, bool dual, int64_t B, int64_t off_lo, int64_t off_hi);
+size_t tc_workspace_bytes(int m, int n, int64_t B, int sms);
+int contract_batched_tc(const BatchedArgs &a, cudaStream_t st);
 extern tk_batched_config g_batched_cfg;
 // resolved batched launch shape; returns false when the kernel does not cover it
 bool batched_resolve(int n, int storage, bool dual, int64_t B, int sms, int smem_optin, tk_batched_config *out);

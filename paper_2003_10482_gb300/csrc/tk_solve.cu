@@ -436,8 +436,15 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
   if (O->method == TK_NEWTON_FULL) {
     unsigned char *base = reinterpret_cast<unsigned char *>(work) + ((tk_solve_workspace_size(P) + 255) & ~size_t(255));
     const FullLayout L = full_layout(P);
-    s.full = true;
+    // without a second tensor every evaluation is a Hessian pass over K (it
+    // gives F and grad F too); with one, F and grad F come from contraction
+    // passes over K and the Hessian of each new point from a pass over K_hvp
+    s.full = P->K_hvp == nullptr;
     s.hws = base + L.hws;
+    // this region's offset in the workspace depends on B: a plan recorded
+    // here by an earlier call may have been overwritten since (by that call's
+    // matrices at another B), so the pass uploads its plan afresh
+    forget_hessian_plan(s.hws);
     s.hws_bytes = L.hcur - L.hws;
     Hcur = reinterpret_cast<double *>(base + L.hcur);
     Htrial = reinterpret_cast<double *>(base + L.htrial);
@@ -562,6 +569,13 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
       std::vector<int> list;
       for (int64_t b = 0; b < B; ++b)
         if (active[b]) list.push_back((int)b);
+      if (!s.full) {
+        for (int b : list) {
+          TK_TRY(tk_hessian(s.m, n, P->hvp_storage_dtype, P->K_hvp, A + (size_t)b * n, Hcur + (size_t)b * n * n, s.hws,
+                            s.hws_bytes, s.st));
+          ++passes[b];
+        }
+      }
       TK_TRY(s.axpby(zero, s.w.g, zero, s.w.g, s.w.p));
       std::vector<double> bad_flag(B, 0.0);
       for (size_t c0 = 0; c0 < list.size(); c0 += kNewtonChunk) {
@@ -601,13 +615,17 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
     TK_TRY(s.axpby(minus1, s.w.g, zero, s.w.g, s.w.at));
     TK_TRY(s.select(flag, s.w.at, s.w.p));
 
-    // Armijo backtracking, all problems in lockstep
+    // Armijo backtracking, all problems in lockstep; a problem whose step has
+    // shrunk 1e8-fold without an accepted point has met its rounding floor
     s.hdst = Htrial;
+    std::vector<double> t_first(t);
     std::vector<char> ls(B);
     std::vector<double> accepted(B, 0.0);
     std::vector<char> real_decrease(B, 0);  // accepted by Armijo's test (a decrease F's rounding cannot fake)
     for (int64_t b = 0; b < B; ++b) ls[b] = active[b];
-    for (int tries = 0; tries < 80; ++tries) {
+    // at most 10 trials: each shrinks the step 2-10-fold (cubic interpolation),
+    // so ten rejections mean F's rounding, not the step, decides
+    for (int tries = 0; tries < 10; ++tries) {
       for (int64_t b = 0; b < B; ++b) {
         ca[b] = 1.0;
         // problems that accepted a step keep it: the shared trial buffers
@@ -640,7 +658,7 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
           real_decrease[b] = armijo && Ft[b] < F[b] - 1e-12 * std::max(1.0, fabs(F[b]));
         } else {
           t[b] = backtrack_step(t[b], F[b], slope[b], Ft[b], slope_t[b]);
-          if (t[b] < 1e-30) {
+          if (t[b] < 1e-8 * t_first[b]) {
             ls[b] = 0;
             stalled[b] = 1;
           } else {

@@ -122,8 +122,8 @@ def test_nystrom_select_rejects_bad_sizes(L):
 def test_batched_config_validation():
     tk = pytest.importorskip("paper_2003_10482_gb300")
     for bad in (dict(vpl=3), dict(block_bytes=1000), dict(block_bytes=4100), dict(nbuf=5), dict(slice_mult=3),
-                dict(min_batch=-1)):
+                dict(min_batch=-1), dict(tensor_cores=2), dict(tensor_cores=-2)):
         with pytest.raises(tk.TKError):
             tk.tk_batched_set_config(**bad)
-    tk.tk_batched_set_config(vpl=1, block_bytes=8320, nbuf=2, slice_mult=2, min_batch=4)
+    tk.tk_batched_set_config(vpl=1, block_bytes=8320, nbuf=2, slice_mult=2, min_batch=4, tensor_cores=-1)
     tk.tk_batched_set_config(reset=True)
