@@ -22,10 +22,11 @@
 //     (c, d) from row min(c, d), lanes running along whichever index is
 //     contiguous in memory -- weights column b, splits it into TF32 hi/lo and
 //     stores both in the K-major 128-byte-swizzled layout;
-//   * one thread issues 4 k-steps x 3 tcgen05.mma (hi.hi + hi.lo + lo.hi,
-//     M = 128 vectors, N = the job's rows, K = 8) into the job's accumulator
-//     columns and commits them to the stage's mbarrier, so the next chunk is
-//     gathered while these run.
+//   * one thread issues 4 k-steps x 3 tcgen05.mma (hi.hi into one
+//     accumulator, hi.lo + lo.hi into a second, so that the large products
+//     are summed apart from the small ones; M = 128 vectors, N = the job's
+//     rows, K = 8) and commits them to the stage's mbarrier, so the next
+//     chunk is gathered while these run.
 // The epilogue reads the accumulator (tcgen05.ld), adds A_Q (M'/m) Rf_c into
 // the block's g accumulator -- 128 x n FP32 values in tensor memory, column
 // c -- and carries the triangle's quadratic-form sum; the triangle's last job
@@ -47,9 +48,10 @@ namespace tk {
 
 constexpr int kTcThreads = 128;
 constexpr int kTcSlice = 128;        // vectors per block (M of the MMA)
-constexpr int kTcMaxN = 320;         // g accumulator columns available beside the job's 96 (+ alignment)
-constexpr int kTcFlushJobs = 256;    // jobs between FP64 flushes of the g accumulator
-constexpr uint32_t kTcAColsG = 128;  // first tensor-memory column of the g accumulator
+constexpr int kTcMaxN = 320;         // g accumulator columns left beside the two job accumulators
+constexpr int kTcFlushJobs = 128;    // jobs between FP64 flushes of the g accumulator
+constexpr uint32_t kTcColsSmall = 96;   // tensor-memory columns: [0, 96) hi*hi', [96, 192) the cross terms,
+constexpr uint32_t kTcAColsG = 192;     // [192, 192 + n16) the g accumulator
 constexpr int kTcAStage = 32768;     // vectors' chunk: hi 16 KB + lo 16 KB
 constexpr int kTcBPart = tc::kRowsPerJob * 128;  // one part (hi or lo) of a row chunk
 constexpr int kTcBStage = 2 * kTcBPart;
@@ -107,31 +109,64 @@ __device__ __forceinline__ float ld_entry(const unsigned char *K, int64_t off) {
 }
 
 // Gather rows [cs, cs + npad) x columns [d0, d0 + 32) of S~_Q into the
-// swizzled hi/lo tiles.  32-row sub-blocks wholly above the diagonal are read
-// along the rows (lanes over d), those wholly below it along the columns of
-// the stored rows (lanes over c); the diagonal sub-blocks either way.
+// swizzled hi/lo tiles.  A thread takes 4 consecutive columns of a row (one
+// 16-byte chunk of the tile) in each of 2 groups of each 32-row sub-block.
+// Sub-blocks wholly below the diagonal put the lanes along the rows (entry
+// (c, d) with d < c sits in stored row d, consecutive c contiguous); the
+// others along the columns (8 lanes per row, consecutive d contiguous).  The
+// in-triangle offset (r - bb)(2n - bb - r + 1)/2 + (s - r), r = min(c, d),
+// s = max(c, d), fits 32 bits (n <= 320).  All loads are issued before the
+// first is used.
 template <typename ST>
 __device__ __forceinline__ void stage_rows(const TcParams &p, const TcTri &tri, int cs, int npad, int d0,
                                            unsigned char *bhi, unsigned char *blo) {
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n = p.n, b = tri.b;
+  constexpr int kSub = tc::kRowsPerJob / 32;
+  const int t = threadIdx.x;
+  const int n = p.n, b = tri.b, bb = b < 0 ? 0 : b;
+  const int span = 2 * n - bb + 1;
+  const ST *__restrict__ Kt = reinterpret_cast<const ST *>(p.K) + tri.base;
+  float x[kSub][2][4];
+#pragma unroll
+  for (int sb = 0; sb < kSub; ++sb) {
+    const int jb = 32 * sb;
+    const bool lower = d0 + 31 < cs + jb;
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      const int j = lower ? jb + (t & 31) : jb + (t >> 3) + 16 * g;
+      const int k4 = lower ? 4 * ((t >> 5) + 4 * g) : 4 * (t & 7);
+      const int c = cs + j;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int d = d0 + k4 + e;
+        const int r = min(c, d), s = max(c, d);
+        const bool ok = j < npad && r >= bb && s < n;
+        const int off = (((r - bb) * (span - r)) >> 1) + (s - r);
+        x[sb][g][e] = ok ? ld_elem<ST, float>(Kt + off) : 0.f;
+      }
+    }
+  }
   const float fb = kInvSmall<float>[tri.kb + 1];
-  const unsigned char *Kt = p.K + tri.base * (int64_t)sizeof(ST);
-  for (int jb = 0; jb < npad; jb += 32) {
-    const bool lower = d0 + 31 < cs + jb;  // every column below every row of the sub-block
-    for (int it = w; it < 32; it += 4) {
-      const int j = lower ? jb + lane : jb + it;
-      const int k = lower ? it : lane;
+  const bool has_b = b >= d0 && b < d0 + 32;
+#pragma unroll
+  for (int sb = 0; sb < kSub; ++sb) {
+    const int jb = 32 * sb;
+    if (jb >= npad) break;
+    const bool lower = d0 + 31 < cs + jb;
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      const int j = lower ? jb + (t & 31) : jb + (t >> 3) + 16 * g;
+      const int k4 = lower ? 4 * ((t >> 5) + 4 * g) : 4 * (t & 7);
       if (j >= npad) continue;
-      const int c = cs + j, d = d0 + k;
-      const int64_t off = tc::sym_entry(n, b, c, d);
-      float x = off >= 0 ? ld_entry<ST>(Kt, off) : 0.f;
-      if (d == b) x *= fb;
-      float hi, lo;
-      umma::split_tf32(x, hi, lo);
-      const uint32_t so = umma::sw128_offset((uint32_t)j, (uint32_t)k);
-      *reinterpret_cast<float *>(bhi + so) = hi;
-      *reinterpret_cast<float *>(blo + so) = lo;
+      float h[4], l[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float v = x[sb][g][e];
+        if (has_b && d0 + k4 + e == b) v *= fb;
+        umma::split_tf32(v, h[e], l[e]);
+      }
+      const uint32_t so = umma::sw128_offset((uint32_t)j, (uint32_t)k4);
+      *reinterpret_cast<float4 *>(bhi + so) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4 *>(blo + so) = make_float4(l[0], l[1], l[2], l[3]);
     }
   }
 }
@@ -147,6 +182,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_batched_kernel(TcParams p) {
                                                         ~uintptr_t(1023));
   unsigned char *sA = sm;                   // [2][hi 16 KB | lo 16 KB]
   unsigned char *sB = sm + 2 * kTcAStage;   // [2][hi 12 KB | lo 12 KB]
+  float *a_rows = reinterpret_cast<float *>(sB + 2 * kTcBStage);  // [96 rows][128 vectors]
   const int tid = threadIdx.x, w = tid >> 5;
   const int m = p.m, n = p.n;
   const int slice = blockIdx.x / p.P, part = blockIdx.x % p.P;
@@ -167,7 +203,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_batched_kernel(TcParams p) {
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tl = tbase + ((uint32_t)(32 * w) << 16);  // this warp's lanes
-  const uint32_t tR = tl, tG = tl + kTcAColsG;
+  const uint32_t tR = tl, tRs = tl + kTcColsSmall, tG = tl + kTcAColsG;
   const float zero16[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   for (int c0 = 0; c0 < p.n16; c0 += 16) tmem_st16(tG + c0, zero16);
   tmem_wait_st();
@@ -184,10 +220,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_batched_kernel(TcParams p) {
   auto flush = [&]() {
     for (int c0 = 0; c0 < p.n16; c0 += 16) {
       float g[16];
+      double old[16];
       umma::tmem_ld16(tG + c0, g);
 #pragma unroll
+      for (int i = 0; i < 16; ++i) old[i] = c0 + i < n ? gp[(size_t)(c0 + i) * kTcSlice + tid] : 0.0;
+#pragma unroll
       for (int i = 0; i < 16; ++i)
-        if (c0 + i < n) gp[(size_t)(c0 + i) * kTcSlice + tid] += (double)g[i];
+        if (c0 + i < n) gp[(size_t)(c0 + i) * kTcSlice + tid] = old[i] + (double)g[i];
       tmem_st16(tG + c0, zero16);
     }
     tmem_wait_st();
@@ -220,12 +259,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_batched_kernel(TcParams p) {
         for (int ks = 0; ks < 4; ++ks) {
           const uint64_t ah = umma::desc_sw128(a0 + 32 * ks), al = umma::desc_sw128(a0 + 16384 + 32 * ks);
           const uint64_t bh = umma::desc_sw128(b0 + 32 * ks), bl = umma::desc_sw128(b0 + kTcBPart + 32 * ks);
-          umma::mma_tf32(tR, ah, bh, idesc, (kc > job.kc0 || ks > 0) ? 1u : 0u);
-          umma::mma_tf32(tR, ah, bl, idesc, 1u);
-          umma::mma_tf32(tR, al, bh, idesc, 1u);
+          const uint32_t acc = (kc > job.kc0 || ks > 0) ? 1u : 0u;
+          umma::mma_tf32(tR, ah, bh, idesc, acc);
+          umma::mma_tf32(tRs, ah, bl, idesc, acc);
+          umma::mma_tf32(tRs, al, bh, idesc, 1u);
         }
         umma::mma_commit(&bar_mma[s]);
       }
+    }
+    // this vector's values at the job's rows, read while the MMAs run
+    for (int j0 = 0; j0 < npad; j0 += 16) {
+      float v[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = cs + j0 + i < n ? atb[(size_t)(cs + j0 + i) * p.Bpad] : 0.f;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) a_rows[(j0 + i) * kTcSlice + tid] = v[i];
     }
     // the job's accumulator is complete once its last chunk's MMAs are
     if (!mbar_wait_bounded(&bar_mma[(gchunk - 1) & 1u], ((gchunk - 1) >> 1) & 1u)) s_bad = 1;
@@ -237,14 +285,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_batched_kernel(TcParams p) {
     const float mprime = (float)tri.mprime;
     const float coef = AQ * mprime * inv_m;
     for (int j0 = 0; j0 < npad; j0 += 16) {
-      float r[16], g[16];
+      float r[16], rs[16], g[16];
       umma::tmem_ld16(tR + j0, r);
+      umma::tmem_ld16(tRs + j0, rs);
       umma::tmem_ld16(tG + cs + j0, g);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) r[i] += rs[i];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int c = cs + j0 + i;
         g[i] += coef * r[i];
-        if (c > b && c < n) P1 += atb[(size_t)c * p.Bpad] * r[i];
+        if (c > b && c < n) P1 += a_rows[(j0 + i) * kTcSlice + tid] * r[i];
         if (c == b) Rfb = r[i];
       }
       tmem_st16(tG + cs + j0, g);
@@ -526,7 +577,8 @@ int contract_batched_tc(const BatchedArgs &a, cudaStream_t st) {
   int slices = 0, P = 0;
   tc_shape(a.B, di.sms, &slices, &P);
   const int nkc = (n + 31) / 32, n16 = (n + 15) & ~15, Bpad = slices * kTcSlice, grid = slices * P;
-  const size_t smem = 1024 + 2 * (size_t)kTcAStage + 2 * (size_t)kTcBStage;
+  const size_t smem = 1024 + 2 * (size_t)kTcAStage + 2 * (size_t)kTcBStage +
+                      (size_t)tc::kRowsPerJob * kTcSlice * sizeof(float);
   if (smem > (size_t)di.smem_optin) return fail(TK_EUNSUPPORTED, "tensor-core batched kernel: shared memory");
   unsigned char *ws = reinterpret_cast<unsigned char *>(a.work);
   size_t njobs = 0, ntris = 0;

@@ -121,3 +121,32 @@ def hessian_bound(n: int, m: int, abs_terms: np.ndarray, storage: str) -> np.nda
     k = max(tri, 64) + 5 + 12 + 3 * m + 8
     u = U64 if storage == "f64" else U32
     return 1.01 * k * u * abs_terms + 1e-300
+
+
+def tc_batched_rel(n: int, m: int) -> float:
+    """Relative bound (times 2 sum |terms|) of the tensor-core batched
+    contraction on an already-rounded K, from its arithmetic:
+      * each product of the 3-term TF32 split misses x*a by at most
+        3.01 * 2^-22 |x a| (lo*lo' and the two residuals of the split), after
+        one rounding of the weighted entry and one of the FP64 vector (2u);
+      * the hi*hi' accumulator sums n + 31 products, the cross-term one twice
+        as many 2^-10-smaller ones, each addition off by at most one FP32 ulp
+        (2u; no rounding mode of the tensor cores assumed), one more rounding
+        joins the two;
+      * the epilogue: A_Q (M'/m) with 2m - 3 roundings plus the product, at
+        most 2 x 128 additions into the FP32 g accumulator between FP64
+        flushes (one row and one prefix addition per job), the quadratic-form
+        sum over <= n rows, about 12 roundings in the triangle's finish and
+        m + 2 in a prefix term.
+    The factor 2 on sum |terms| covers the quadratic form: its absolute
+    counterpart counts the column-b pairs twice (once in the row sum P, once
+    in the a_b r_b correction)."""
+    u = U32
+    e_prod = 3.01 * 2.0 ** -22 + 2 * u
+    e_acc = 2 * u * (n + 31) * (1 + 2.0 ** -9) + u
+    e_epi = u * ((2 * m - 2) + 2 * 128 + n + 12 + (m + 2))
+    return e_prod + e_acc + e_epi
+
+
+def tc_batched_bound(abs_terms: np.ndarray, n: int, m: int) -> np.ndarray:
+    return 2.0 * tc_batched_rel(n, m) * abs_terms + 1e-30

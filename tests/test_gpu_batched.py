@@ -5,7 +5,8 @@ import torch
 
 import oracle
 import synth
-from gpu_util import U32, as_f64, batched_accumulation_depth, batched_bound, round_storage
+from gpu_util import U32, as_f64, batched_accumulation_depth, batched_bound, round_storage, tc_batched_bound, \
+    tc_batched_rel
 
 pytestmark = pytest.mark.gpu
 
@@ -93,3 +94,76 @@ def test_batched_full_width_against_closed_form(path_tensor):
     assert np.all(np.abs(G - g_ref) <= rel * g_abs), float(np.max(np.abs(G - g_ref) / (rel * g_abs)))
     assert np.all(np.abs(S - S_ref) <= rel * S_abs)
     assert np.all(np.abs(HV - h_ref) <= rel_h * h_abs), float(np.max(np.abs(HV - h_ref) / (rel_h * h_abs)))
+
+
+@pytest.fixture
+def tensor_cores():
+    """Route batched K[a^{m-1}] passes to the tensor-core kernel wherever it covers them."""
+    tk.tk_batched_set_config(tensor_cores=1)
+    yield
+    tk.tk_batched_set_config(reset=True)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("m,n,d,B,vdt", [(4, 70, 3, 130, torch.float64), (3, 130, 2, 128, torch.float32),
+                                         (4, 33, 4, 256, torch.float64), (2, 150, 3, 200, torch.float64),
+                                         (4, 101, 3, 300, torch.float32), (5, 24, 3, 129, torch.float64),
+                                         (4, 5, 2, 128, torch.float64)])
+def test_tensor_core_contraction_matches_oracle(tensor_cores, m, n, d, B, vdt, storage):
+    # the tcgen05 pass (TF32 with the 3-term split, FP32 and FP64 partials)
+    # element by element against the oracle, for vectors of every slice of
+    # 128, including a partial last slice
+    X = synth.small_problem(m, n, d, salt=840 + n)
+    Kt = round_storage(oracle.build(X, m), storage)
+    Kr = as_f64(Kt)
+    A = synth.alpha_like(n, salt=841, batch=B)
+    assert tk.tk_batched_get_config(m, n, storage, False, B)["tensor_cores"] == 1
+    Ad = torch.tensor(A, device="cuda").to(vdt)
+    a_used = Ad.double().cpu().numpy()
+    G, S = tk.tk_contract(Kt.cuda(), m, n, Ad)
+    G, S = G.double().cpu().numpy(), S.cpu().numpy()
+    assert np.all(np.isfinite(G)) and np.all(np.isfinite(S))
+    pick = sorted(set([0, 1, 127, min(B - 1, 128), B // 2, B - 2, B - 1]))
+    for b in pick:
+        g_ref, S_ref = oracle.contract(Kr, a_used[b], m)
+        g_abs, S_abs = oracle.contract(np.abs(Kr), np.abs(a_used[b]), m)
+        tol = tc_batched_bound(g_abs, n, m)
+        if vdt == torch.float32:
+            tol = tol + U32 * np.abs(g_ref)  # G rounded to the vector type
+        assert np.all(np.abs(G[b] - g_ref) <= tol), (b, float(np.max(np.abs(G[b] - g_ref) / tol)))
+        assert abs(S[b] - S_ref) <= float(tc_batched_bound(np.array([S_abs]), n, m)[0]), b
+
+
+def test_tensor_core_full_width_against_closed_form(path_tensor, tensor_cores):
+    # all 512 vectors of the batched workload (m = 4, n' = 300, FP32) in one
+    # tensor-core pass against the closed forms, and the time of one pass
+    # beside the SIMT batched kernel's
+    m, X, K = path_tensor
+    n, d = X.shape
+    B = 512
+    A = synth.alpha_like(n, salt=850, batch=B)
+    Ad = torch.tensor(A, device="cuda")
+    assert tk.tk_batched_get_config(m, n, "f32", False, B)["tensor_cores"] == 1
+    G, S = tk.tk_contract(K, m, n, Ad)
+    G, S = G.cpu().numpy(), S.cpu().numpy()
+    U, Ua = A @ X, np.abs(A) @ np.abs(X)
+    g_ref, g_abs = (U ** 3) @ X.T, (Ua ** 3) @ np.abs(X).T
+    S_ref, S_abs = np.sum(U ** 4, axis=1), np.sum(Ua ** 4, axis=1)
+    rel = 1.01 * (d + m + 2) * U32 + 2.0 * tc_batched_rel(n, m)
+    err = np.abs(G - g_ref) / g_abs
+    print(f"\ntensor-core pass: max |err| / sum|terms| = {float(np.max(err)):.3e} (bound {rel:.3e})")
+    assert np.all(np.abs(G - g_ref) <= rel * g_abs), float(np.max(np.abs(G - g_ref) / (rel * g_abs)))
+    assert np.all(np.abs(S - S_ref) <= rel * S_abs)
+    times = {}
+    for mode in (1, -1):
+        tk.tk_batched_set_config(tensor_cores=mode)
+        tk.tk_contract(K, m, n, Ad)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            tk.tk_contract(K, m, n, Ad)
+        e1.record()
+        e1.synchronize()
+        times[mode] = e0.elapsed_time(e1) / 3
+    print(f"one B=512 pass: tensor cores {times[1]:.2f} ms, SIMT batched kernel {times[-1]:.2f} ms")
