@@ -249,22 +249,25 @@ def run_reference(args) -> None:
 
 def batched_leg(dev) -> dict:
     """Dual solves/s of the batched FP32 path against plain FP64 solves, on the
-    whole lambda path.
+    whole lambda path, and the batched contraction pass behind it.
 
     Workload: m = 4, n' = 300 Nystrom landmarks (uniform without replacement,
     tk_nystrom_select) of 20,000 points, d = 80; lambda in logspace(-4, 0, 64)
     x 8 cross-validation folds (masks) = 512 problems.  Both arms use the
     full-Hessian Newton method (FP64 Cholesky on the device) to the same
-    relative-gap target (1e-7) with the same 12-iteration cap, starting from
-    the best multiple of y: batched = one tk_solve_dual call over all 512
-    problems on the FP32 tensor (objective and gradient of every active
-    problem from one batched contraction pass, the Newton matrix of each new
-    point from its Hessian pass); plain = one call per problem on the FP64
-    tensor (F and grad F from FP64 contraction passes, the Newton matrix from a
-    Hessian pass over the FP32 copy), for fold 0 of every lambda (64 problems).
-    Accuracy: F of the batched solution of each of those problems under the
-    FP64 tensor against its plain FP64 solve.  Reported per lambda, with the
-    convergence and passes of every fold."""
+    relative-gap target (1e-7), at most 30 iterations, and the same
+    continuation along the path: the 64 lambdas are taken largest first in 8
+    stages of 8; stage 0 starts from the best multiple of y, every later
+    problem from the same fold's solution at the previous stage's smallest
+    lambda.  Batched = one tk_solve_dual call per stage over its 64 problems
+    on the FP32 tensor (objective and gradient of the active problems from one
+    batched contraction pass, the Newton matrix of each new point from its
+    Hessian pass); plain = one call per problem on the FP64 tensor (F, grad F
+    and the Newton matrix all from FP64 passes), for fold 0 of every lambda
+    (64 problems).  A problem whose Newton matrix fails to factorise stops
+    there (its stored tensor's rounding has made the form indefinite).  Accuracy: F of
+    each fold-0 batched solution under the FP64 tensor against its plain FP64
+    solve, per lambda, with the convergence and passes of every fold."""
     import torch
 
     import paper_2003_10482_gb300 as tk
@@ -278,50 +281,125 @@ def batched_leg(dev) -> dict:
     lam = torch.tensor(p["lambdas"], device=dev)
     mask = torch.tensor(p["masks"], device=dev)
     B = lam.numel()
+    folds, nlam = 8, B // 8
     K32 = tk.tk_build_packed(X, m, storage="f32")
     K64 = tk.tk_build_packed(X, m, storage="f64")
-    gap, iters = 1e-7, 12
+    gap, iters = 1e-7, 30
+
+    # the batched contraction pass itself at B = 512: tensor cores vs SIMT
+    A512 = torch.tensor(synth.alpha_like(n, salt=5, batch=B), device=dev)
+    passes = {}
+    for mode, name in ((1, "tensor_cores"), (-1, "simt")):
+        tk.tk_batched_set_config(tensor_cores=mode)
+        tk.tk_contract(K32, m, n, A512)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            tk.tk_contract(K32, m, n, A512)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / 3
+        passes[name] = {"ms": ms, "tflops": 4.0 * B * K32.numel() / ms / 1e9}
+    tk.tk_batched_set_config(reset=True)
+    tf32_peak = 1879.2 * 1.1 / 2.25  # measured bf16 burst x nominal TF32/BF16 ratio
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            tf32_peak = json.load(f)["bf16_tflops"] * 1.1 / 2.25
+    except (OSError, KeyError, ValueError):
+        pass
+    contraction = {"B": B, "entries": int(K32.numel()), "flops_per_entry": 4 * B, **passes,
+                   "speedup_tensor_cores": passes["simt"]["ms"] / passes["tensor_cores"]["ms"],
+                   "tf32_peak_tflops": tf32_peak,
+                   "frac_of_tf32_peak": passes["tensor_cores"]["tflops"] / tf32_peak,
+                   "peak_note": "measured bf16 burst x nominal TF32/BF16 ratio (1.1 / 2.25); the pass does 3 TF32 "
+                                "products per FP32 product (the split), so useful flops are a third of the tensor work"}
+
+    order = list(range(nlam - 1, -1, -1))           # lambda indices, largest first
+    stages = [order[k:k + 8] for k in range(0, nlam, 8)]
     # warm-up (library load, plans, workspaces)
-    tk.tk_solve_dual(K32, m, n, y, lam[:32], mask=mask[:32], method="newton_full", tol=0.0, rel_gap=gap, max_iter=1,
-                     K_hvp=K32, start_on_y=True)
+    tk.tk_solve_dual(K32, m, n, y, lam[:64], mask=mask[:64], method="newton_full", tol=0.0, rel_gap=gap,
+                     max_iter=1, K_hvp=K32, start_on_y=True)
     tk.tk_solve_dual(K64, m, n, y, lam[:1], mask=mask[:1], method="newton_full", tol=0.0, rel_gap=gap, max_iter=1,
-                     K_hvp=K32, start_on_y=True)
+                     K_hvp=K64, start_on_y=True)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    A32, rep, _ = tk.tk_solve_dual(K32, m, n, y, lam, mask=mask, method="newton_full", tol=0.0, rel_gap=gap,
-                                   max_iter=iters, K_hvp=K32, start_on_y=True)
-    torch.cuda.synchronize()
-    t_batched = time.perf_counter() - t0
-    # the plain FP64 arm: fold 0 of every lambda (64 problems)
-    plain = list(range(0, B, 8))
-    t_plain, F64, rep64 = 0.0, {}, {}
-    for j in plain:
+
+    def probs(st):
+        return [8 * i + f for i in st for f in range(folds)]
+
+    # batched arm: one call per stage
+    A32 = torch.zeros(B, n, dtype=torch.float64, device=dev)
+    rep = [None] * B
+    t_batched = 0.0
+    t_stage_b, t_stage_p = [], []
+    prev = None
+    for st in stages:
+        js = probs(st)
+        a0 = None if prev is None else torch.stack([A32[8 * prev + (j % 8)] for j in js])
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, r64, _ = tk.tk_solve_dual(K64, m, n, y, lam[j:j + 1], mask=mask[j:j + 1], method="newton_full",
-                                     tol=0.0, rel_gap=gap, max_iter=iters, K_hvp=K32, start_on_y=True)
+        A, r, _ = tk.tk_solve_dual(K32, m, n, y, lam[js], alpha0=a0, mask=mask[js], method="newton_full", tol=0.0,
+                                   rel_gap=gap, max_iter=iters, K_hvp=K32, start_on_y=prev is None)
         torch.cuda.synchronize()
-        t_plain += time.perf_counter() - t0
-        F64[j] = r64[0]["F"]
-        rep64[j] = r64[0]
+        t_stage_b.append(time.perf_counter() - t0)
+        t_batched += t_stage_b[-1]
+        A32[js] = A
+        for j, rr in zip(js, r):
+            rep[j] = rr
+        prev = st[-1]
+    # plain FP64 arm: fold 0, one problem per call, the same starts
+    t_plain, F64, rep64 = 0.0, {}, {}
+    A64 = {}
+    prev = None
+    for st in stages:
+        t_stage_p.append(0.0)
+        for i in st:
+            j = 8 * i
+            a0 = None if prev is None else A64[8 * prev].reshape(1, n)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            A, r64, _ = tk.tk_solve_dual(K64, m, n, y, lam[j:j + 1], alpha0=a0, mask=mask[j:j + 1],
+                                         method="newton_full", tol=0.0, rel_gap=gap, max_iter=iters, K_hvp=K64,
+                                         start_on_y=prev is None)
+            torch.cuda.synchronize()
+            t_stage_p[-1] += time.perf_counter() - t0
+            t_plain += time.perf_counter() - t0
+            A64[j] = A[0]
+            F64[j] = r64[0]["F"]
+            rep64[j] = r64[0]
+        prev = st[-1]
+    plain = sorted(F64)
     # the batched solutions of those problems judged under the FP64 tensor
     Fb, _, _ = tk.tk_objective(K64, m, n, A32[plain].contiguous(), y, lam[plain].contiguous())
     Fb = Fb.cpu().numpy()
     errs = {j: abs(float(Fb[i]) - F64[j]) / max(abs(F64[j]), 1e-300) for i, j in enumerate(plain)}
     per_lambda = []
     lam_h = p["lambdas"]
-    for i in range(0, B, 8):
-        js = range(i, i + 8)
-        per_lambda.append({"lambda": float(lam_h[i]),
-                           "rel_obj_diff_vs_fp64_fold0": errs[i],
-                           "fp64_fold0_converged": rep64[i]["status"] == 0,
-                           "fp64_fold0_passes": rep64[i]["passes"],
+    for i in range(nlam):
+        js = range(8 * i, 8 * i + 8)
+        per_lambda.append({"lambda": float(lam_h[8 * i]),
+                           "rel_obj_diff_vs_fp64_fold0": errs[8 * i],
+                           "fp32_reaches_fp64_within_1e-6": errs[8 * i] <= 1e-6,
+                           "fp64_fold0_converged": rep64[8 * i]["status"] == 0,
+                           "fp64_fold0_passes": rep64[8 * i]["passes"],
                            "fp32_converged_folds": sum(rep[j]["status"] == 0 for j in js),
                            "fp32_passes_max": max(rep[j]["passes"] for j in js)})
     ok = [j for j in plain if errs[j] <= 1e-6]
+    lam_ok = [float(lam_h[j]) for j in ok]
     held_out = float(A32[~mask.bool()].abs().max()) if bool((~mask.bool()).any()) else 0.0
+    # equal accuracy: the lambdas whose FP32 solutions reach the FP64 objective,
+    # and the stages made only of such lambdas (timed as a whole in both arms)
+    ok_set = {j // 8 for j in ok}
+    eq_b = [j for j in range(B) if j // 8 in ok_set]
+    eq_stages = [k for k, st in enumerate(stages) if all(i in ok_set for i in st)]
+    tb = sum(t_stage_b[k] for k in eq_stages)
+    tp = sum(t_stage_p[k] for k in eq_stages)
+    eq_speedup = (64 * len(eq_stages) / tb) / (8 * len(eq_stages) / tp) if eq_stages else None
     return {"workload": "batched_path_m4_np300_d80: 64 lambdas in [1e-4, 1] x 8 folds = 512 problems",
-            "problems": B, "method": "newton_full (Hessian pass + FP64 Cholesky per problem and iteration)",
+            "problems": B, "method": "newton_full (Hessian pass + FP64 Cholesky per problem and iteration), "
+                                     "continuation in 8 stages of 8 lambdas, largest first",
+            "stage_seconds": {"batched_fp32": t_stage_b, "plain_fp64_fold0": t_stage_p},
+            "batched_contraction_pass": contraction,
             "batched_fp32": {"solves_per_s": B / t_batched, "seconds": t_batched,
                              "converged": sum(r["status"] == 0 for r in rep),
                              "passes_total": sum(r["passes"] for r in rep),
@@ -331,7 +409,15 @@ def batched_leg(dev) -> dict:
                            "converged": sum(r["status"] == 0 for r in rep64.values()),
                            "passes_total": sum(r["passes"] for r in rep64.values())},
             "speedup": (B / t_batched) / (len(plain) / t_plain),
-            "target": "relative objective gap 1e-7 (Newton decrement), at most 12 Newton iterations",
+            "target": f"relative objective gap {gap:g} (Newton decrement), at most {iters} Newton iterations",
+            "equal_accuracy": {"lambdas": len(ok_set), "lambda_min": min(lam_ok) if lam_ok else None,
+                               "problems": len(eq_b), "stages": eq_stages,
+                               "batched_solves_per_s": 64 * len(eq_stages) / tb if eq_stages else None,
+                               "plain_fp64_solves_per_s": 8 * len(eq_stages) / tp if eq_stages else None,
+                               "speedup": eq_speedup,
+                               "note": "lambdas whose fold-0 FP32 solution is within 1e-6 of the FP64 objective; "
+                                       "below them the FP32 tensor's rounding (indefinite along null(X^T), where "
+                                       "alpha grows like 1/lambda) decides the FP32 solution"},
             "fold0_within_1e-6_of_fp64": len(ok),
             "fold0_max_rel_obj_diff_vs_fp64": max(errs.values()), "held_out_max_abs_alpha": held_out,
             "per_lambda": per_lambda}

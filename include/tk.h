@@ -477,9 +477,12 @@ size_t tk_solve_workspace_size_opts(const tk_problem *P, const tk_solve_opts *O)
  *               (K[a^{m-1}] = K[a^{m-2}] a, K[a^m] = a . K[a^{m-1}]) also gives F
  *               and grad F, so an accepted step costs one pass; with K_hvp the
  *               evaluations are contraction passes over K and each new point's
- *               Hessian is one pass over K_hvp.  The same backtracking; a problem
- *               whose H is not positive definite (a rounded tensor) takes the
- *               steepest-descent direction that iteration;
+ *               Hessian is one pass over K_hvp.  The same backtracking.  H is
+ *               positive definite for a tensor kernel of even order, so a
+ *               problem whose H fails to factorise (a rounded tensor whose form
+ *               has turned indefinite at the iterate, as FP32/BF16 storage does
+ *               along null(X^T) when |a| grows like 1/lambda) stops there with
+ *               TK_ENOTCONV;
  *   GD_BT:      steepest descent with Armijo backtracking, step initialised
  *               from the previous accepted step.
  * A line search takes at most 10 trials (the cubic interpolation shrinks the

@@ -577,7 +577,6 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
         }
       }
       TK_TRY(s.axpby(zero, s.w.g, zero, s.w.g, s.w.p));
-      std::vector<double> bad_flag(B, 0.0);
       for (size_t c0 = 0; c0 < list.size(); c0 += kNewtonChunk) {
         const int nb = (int)std::min<size_t>(kNewtonChunk, list.size() - c0);
         TK_CUDA_CHECK(cudaMemcpyAsync(s.hidx, list.data() + c0, nb * sizeof(int), cudaMemcpyHostToDevice, s.st));
@@ -585,13 +584,16 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
         TK_TRY(newton_directions(s.m, n, nb, s.hidx, Hcur, P->lambda, P->mask, s.w.g, s.w.p, nws, bad.data(), s.st));
         for (int j = 0; j < nb; ++j)
           if (bad[j]) {
-            bad_flag[list[c0 + j]] = 1.0;
-            indefinite[list[c0 + j]] = 1;
+            // (m-1) K[a^{m-2}] + lambda I is positive definite for a tensor
+            // kernel of even order: a failed factorisation shows that the
+            // stored tensor's rounding has broken the form at this iterate,
+            // where F has no minimiser to approach; the problem stops here
+            const int b = list[c0 + j];
+            indefinite[b] = 1;
+            active[b] = 0;
+            stalled[b] = 1;
           }
       }
-      // a form that is not positive definite (rounded tensor): steepest descent
-      TK_TRY(s.axpby(minus1, s.w.g, zero, s.w.g, s.w.at));
-      TK_TRY(s.select(bad_flag, s.w.at, s.w.p));
       for (int64_t b = 0; b < B; ++b) t[b] = 1.0;
     } else {
       TK_TRY(s.axpby(minus1, s.w.g, zero, s.w.g, s.w.p));
