@@ -622,6 +622,42 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
+def run_case(args) -> None:
+    """One kernel a few times on the batched workload's tensor (m = 4, n' = 300
+    landmarks, FP32), for profiler captures: `hessian` runs tk_hessian,
+    `batched_pass` the B-vector contraction (tensor-core pass unless --tc -1).
+    Prints the mean CUDA-event time per call."""
+    import torch
+
+    import paper_2003_10482_gb300 as tk
+    import synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    p = synth.batched_path()
+    m = p["m"]
+    idx = tk.tk_nystrom_select(p["X"].shape[0], p["n_prime"], p["select_seed"])
+    X = torch.tensor(p["X"][idx], device=dev)
+    n = X.shape[0]
+    K = tk.tk_build_packed(X, m, storage="f32")
+    if args.case == "hessian":
+        a = torch.tensor(synth.alpha_like(n, salt=3), device=dev)
+        call = lambda: tk.tk_hessian(K, m, n, a)  # noqa: E731
+    else:
+        tk.tk_batched_set_config(tensor_cores=args.tc)
+        A = torch.tensor(synth.alpha_like(n, salt=5, batch=args.B), device=dev)
+        call = lambda: tk.tk_contract(K, m, n, A)  # noqa: E731
+    call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        call()
+    e1.record()
+    e1.synchronize()
+    print(json.dumps({"case": args.case, "B": args.B if args.case != "hessian" else 1, "tensor_cores": args.tc,
+                      "ms_per_call": e0.elapsed_time(e1) / 3, "entries": int(K.numel())}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -633,8 +669,14 @@ def main():
                     help="skip the batched-vs-FP64 dual-solve comparison")
     ap.add_argument("--n", type=int, default=0,
                     help="points of the workload (default: all 400); smaller n for profiler captures")
+    ap.add_argument("--case", choices=["hessian", "batched_pass"], default=None,
+                    help="run one kernel on the batched workload's tensor (profiler captures) and exit")
+    ap.add_argument("--B", type=int, default=128, help="vectors of --case batched_pass")
+    ap.add_argument("--tc", type=int, default=1, choices=[1, -1], help="--case batched_pass: tensor cores or SIMT")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.case is not None:
+        run_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.gpus > 1 and "WORLD_SIZE" not in os.environ:
         sys.exit(_spawn_ranks(args.gpus))
