@@ -46,15 +46,20 @@
 
 namespace tk {
 
-constexpr int kTcThreads = 256;     // 8 warps: warps w and w + 4 share tensor-memory lanes 32 (w mod 4) ..
+constexpr int kTcEpiWarps = 4;       // warps 0-3: epilogue, thread i <-> tensor-memory lane i <-> vector i
+constexpr int kTcGatherWarps = 8;    // warps 4-11: gather the rows of S~_Q into the stage ring
+constexpr int kTcGatherThreads = 32 * kTcGatherWarps;
+constexpr int kTcThreads = 32 * (kTcEpiWarps + kTcGatherWarps + 1);  // + warp 12: issues the MMAs
 constexpr int kTcSlice = 128;        // vectors per block (M of the MMA)
 constexpr int kTcMaxN = 320;         // g accumulator columns left beside the two job accumulators
 constexpr int kTcFlushJobs = 128;    // jobs between FP64 flushes of the g accumulator
-constexpr uint32_t kTcColsSmall = 96;   // tensor-memory columns: [0, 96) hi*hi', [96, 192) the cross terms,
-constexpr uint32_t kTcAColsG = 192;     // [192, 192 + n16) the g accumulator
-constexpr int kTcAStage = 32768;     // vectors' chunk: hi 16 KB + lo 16 KB
+constexpr uint32_t kTcAccCols = 96;  // tensor-memory columns: [0, 96) and [96, 192) the two job accumulators,
+constexpr uint32_t kTcAColsG = 192;  // [192, 192 + n16) the g accumulator
+constexpr int kTcStages = 3;         // ring of stages, each: vectors' chunk (hi, lo) + rows' chunk (hi, lo)
+constexpr int kTcAPart = 16384;      // 128 vectors x 32 values x 4 bytes
+constexpr int kTcAStage = 2 * kTcAPart;
 constexpr int kTcBPart = tc::kRowsPerJob * 128;  // one part (hi or lo) of a row chunk
-constexpr int kTcBStage = 2 * kTcBPart;
+constexpr int kTcStageBytes = kTcAStage + 2 * kTcBPart;
 
 struct TcJob {
   int32_t tri;
@@ -118,9 +123,8 @@ __device__ __forceinline__ float ld_entry(const unsigned char *K, int64_t off) {
 // fits 32 bits (n <= 320).  All loads are issued before the first is used.
 template <typename ST>
 __device__ __forceinline__ void stage_rows(const TcParams &p, const TcTri &tri, int cs, int npad, int d0,
-                                           unsigned char *bhi, unsigned char *blo) {
+                                           unsigned char *bhi, unsigned char *blo, int t) {
   constexpr int kSub = tc::kRowsPerJob / 32;
-  const int t = threadIdx.x;
   const int n = p.n, b = tri.b, bb = b < 0 ? 0 : b;
   const int span = 2 * n - bb + 1;
   const ST *__restrict__ Kt = reinterpret_cast<const ST *>(p.K) + tri.base;
@@ -182,33 +186,45 @@ __device__ __forceinline__ void stage_rows(const TcParams &p, const TcTri &tri, 
   }
 }
 
+// Bounded wait on an mbarrier phase; once any wait of the block has run out
+// every later wait returns false at once, so all roles leave their loops.
+__device__ __forceinline__ bool tc_wait(uint64_t *bar, uint32_t parity, volatile int *bad) {
+  if (*bad) return false;
+  if (mbar_wait_bounded(bar, parity)) return true;
+  *bad = 1;
+  return false;
+}
+
 template <typename ST>
 __global__ void __launch_bounds__(kTcThreads, 1) tc_batched_kernel(TcParams p) {
   extern __shared__ unsigned char tc_smem_raw[];
-  __shared__ uint64_t bar_a[2], bar_mma[2];
+  // ring: full (gathered rows written: 256 arrivals), afull (vectors' chunk
+  // landed: the bulk copy's bytes), empty (the MMAs that read the stage are
+  // done: a commit); job accumulators: accf (a job's MMAs are done: a
+  // commit), acce (the epilogue has read the accumulator: 128 arrivals)
+  __shared__ uint64_t bar_full[kTcStages], bar_afull[kTcStages], bar_empty[kTcStages], bar_accf[2], bar_acce[2];
   __shared__ uint32_t tbase;
   __shared__ int s_bad;
-  __shared__ float comb[2][kTcSlice];  // the upper half's triangle sums, handed to the lower half
   if (plan_is_stale(p.status, p.m, p.n, p.P, -2, -2)) return;
   unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) &
                                                         ~uintptr_t(1023));
-  unsigned char *sA = sm;                   // [2][hi 16 KB | lo 16 KB]
-  unsigned char *sB = sm + 2 * kTcAStage;   // [2][hi 12 KB | lo 12 KB]
-  float *a_rows = reinterpret_cast<float *>(sB + 2 * kTcBStage);  // [96 rows][128 vectors]
   const int tid = threadIdx.x, w = tid >> 5;
-  const int vl = tid & (kTcSlice - 1);  // vector of the slice = tensor-memory lane (32 (w mod 4) + lane)
-  const int half = w >> 2;              // which 16-column chunks of a job this thread takes
   const int m = p.m, n = p.n;
   const int slice = blockIdx.x / p.P, part = blockIdx.x % p.P;
-  const int beta = slice * kTcSlice + vl;
+  const int j_lo = p.range[part], j_hi = p.range[part + 1];
   if (w == 0) {
     umma::tmem_alloc(&tbase, 512);
     umma::tmem_relinquish();
   }
   if (tid == 0) {
-    for (int s = 0; s < 2; ++s) {
-      mbar_init(&bar_a[s], 1);
-      mbar_init(&bar_mma[s], 1);
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(&bar_full[s], kTcGatherThreads);
+      mbar_init(&bar_afull[s], 1);
+      mbar_init(&bar_empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&bar_accf[b], 1);
+      mbar_init(&bar_acce[b], 32 * kTcEpiWarps);
     }
     fence_barrier_init();
     s_bad = 0;
@@ -216,123 +232,78 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_batched_kernel(TcParams p) {
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
-  const uint32_t tl = tbase + ((uint32_t)(32 * (w & 3)) << 16);  // this warp's lanes
-  const uint32_t tR = tl, tRs = tl + kTcColsSmall, tG = tl + kTcAColsG;
-  const float zero16[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int c0 = 16 * half; c0 < p.n16; c0 += 32) tmem_st16(tG + c0, zero16);
-  tmem_wait_st();
-  double *gp = p.gpart + (size_t)blockIdx.x * p.n16 * kTcSlice;
-  for (int c = half; c < n; c += 2) gp[(size_t)c * kTcSlice + vl] = 0.0;
-  const float *atb = p.at + beta;  // a[beta][d] at atb[d * Bpad]
-  const float inv_m = 1.f / (float)m;
-  double S64 = 0.0;
-  float Sacc = 0.f, P1 = 0.f, Rfb = 0.f;
-  uint32_t gchunk = 0;
-  int since_flush = 0;
-  const uint32_t idesc_base = umma::idesc_tf32(kTcSlice, 16) & ~(0x3Fu << 17);
+  volatile int *bad = &s_bad;
 
-  // g accumulator -> the block's FP64 partial (each half its own 16-column chunks)
-  auto flush = [&]() {
-    for (int c0 = 16 * half; c0 < p.n16; c0 += 32) {
-      float g[16];
-      double old[16];
-      umma::tmem_ld16(tG + c0, g);
-#pragma unroll
-      for (int i = 0; i < 16; ++i) old[i] = c0 + i < n ? gp[(size_t)(c0 + i) * kTcSlice + vl] : 0.0;
-#pragma unroll
-      for (int i = 0; i < 16; ++i)
-        if (c0 + i < n) gp[(size_t)(c0 + i) * kTcSlice + vl] = old[i] + (double)g[i];
-      tmem_st16(tG + c0, zero16);
-    }
+  if (w < kTcEpiWarps) {
+    // ---------------------------------------------------------------- epilogue
+    const int vl = tid;  // vector of the slice = tensor-memory lane
+    const int beta = slice * kTcSlice + vl;
+    const uint32_t tl = tbase + ((uint32_t)(32 * w) << 16);
+    const uint32_t tG = tl + kTcAColsG;
+    const float zero16[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int c0 = 0; c0 < p.n16; c0 += 16) tmem_st16(tG + c0, zero16);
     tmem_wait_st();
-    S64 += (double)Sacc;
-    Sacc = 0.f;
-  };
-
-  for (int jx = p.range[part]; jx < p.range[part + 1]; ++jx) {
-    const TcJob job = p.jobs[jx];
-    const TcTri tri = p.tris[job.tri];
-    const int b = tri.b, cs = job.cs, npad = job.npad;
-    const uint32_t idesc = idesc_base | ((uint32_t)(npad >> 3) << 17);
-    for (int kc = job.kc0; kc < p.nkc; ++kc, ++gchunk) {
-      const int s = (int)(gchunk & 1u);
-      unsigned char *a_st = sA + s * kTcAStage, *b_st = sB + s * kTcBStage;
-      // the MMAs that read this stage two chunks ago must be done
-      if (gchunk >= 2 && !mbar_wait_bounded(&bar_mma[s], ((gchunk - 2) >> 1) & 1u)) s_bad = 1;
-      if (tid == 0) {
-        mbar_expect_tx(&bar_a[s], kTcAStage);
-        bulk_g2s(a_st, p.img + ((size_t)slice * p.nkc + kc) * (kTcAStage / 4), kTcAStage, &bar_a[s]);
-      }
-      stage_rows<ST>(p, tri, cs, npad, 32 * kc, b_st, b_st + kTcBPart);
-      fence_proxy_async();
-      __syncthreads();
-      if (tid == 0) {
-        if (!mbar_wait_bounded(&bar_a[s], (gchunk >> 1) & 1u)) s_bad = 1;
-        umma::fence_after_sync();
-        const uint32_t a0 = saddr(a_st), b0 = saddr(b_st);
+    double *gp = p.gpart + (size_t)blockIdx.x * p.n16 * kTcSlice;
+    for (int c = 0; c < n; ++c) gp[(size_t)c * kTcSlice + vl] = 0.0;
+    const float *atb = p.at + beta;  // a[beta][d] at atb[d * Bpad]
+    const float inv_m = 1.f / (float)m;
+    double S64 = 0.0;
+    float Sacc = 0.f, P1 = 0.f, Rfb = 0.f;
+    int since_flush = 0;
+    auto flush = [&]() {
+      for (int c0 = 0; c0 < p.n16; c0 += 16) {
+        float g[16];
+        double old[16];
+        umma::tmem_ld16(tG + c0, g);
 #pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          const uint64_t ah = umma::desc_sw128(a0 + 32 * ks), al = umma::desc_sw128(a0 + 16384 + 32 * ks);
-          const uint64_t bh = umma::desc_sw128(b0 + 32 * ks), bl = umma::desc_sw128(b0 + kTcBPart + 32 * ks);
-          const uint32_t acc = (kc > job.kc0 || ks > 0) ? 1u : 0u;
-          umma::mma_tf32(tR, ah, bh, idesc, acc);
-          umma::mma_tf32(tRs, ah, bl, idesc, acc);
-          umma::mma_tf32(tRs, al, bh, idesc, 1u);
-        }
-        umma::mma_commit(&bar_mma[s]);
-      }
-    }
-    // this vector's values at this thread's rows of the job, read while the MMAs run
-    for (int j0 = 16 * half; j0 < npad; j0 += 32) {
-      float v[16];
+        for (int i = 0; i < 16; ++i) old[i] = c0 + i < n ? gp[(size_t)(c0 + i) * kTcSlice + vl] : 0.0;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) v[i] = cs + j0 + i < n ? atb[(size_t)(cs + j0 + i) * p.Bpad] : 0.f;
-#pragma unroll
-      for (int i = 0; i < 16; ++i) a_rows[(j0 + i) * kTcSlice + vl] = v[i];
-    }
-    float AQ = 1.f;
-    for (int j = 0; j < tri.nq; ++j) AQ *= atb[(size_t)tri.q[j] * p.Bpad];
-    const float mprime = (float)tri.mprime;
-    const float coef = AQ * mprime * inv_m;
-    // the job's accumulator is complete once its last chunk's MMAs are
-    if (!mbar_wait_bounded(&bar_mma[(gchunk - 1) & 1u], ((gchunk - 1) >> 1) & 1u)) s_bad = 1;
-    umma::fence_after_sync();
-
-    // epilogue: g_c += A_Q (M'/m) Rf_c; the triangle's quadratic-form sums
-    for (int j0 = 16 * half; j0 < npad; j0 += 32) {
-      uint32_t ur[16], urs[16], ug[16];
-      umma::tmem_ld16_async(tR + j0, ur);
-      umma::tmem_ld16_async(tRs + j0, urs);
-      umma::tmem_ld16_async(tG + cs + j0, ug);
-      umma::tmem_wait_ld();
-      float r[16], g[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        r[i] = __uint_as_float(ur[i]) + __uint_as_float(urs[i]);
-        g[i] = __uint_as_float(ug[i]);
+        for (int i = 0; i < 16; ++i)
+          if (c0 + i < n) gp[(size_t)(c0 + i) * kTcSlice + vl] = old[i] + (double)g[i];
+        tmem_st16(tG + c0, zero16);
       }
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int c = cs + j0 + i;
-        g[i] += coef * r[i];
-        if (c > b && c < n) P1 += a_rows[(j0 + i) * kTcSlice + vl] * r[i];
-        if (c == b) Rfb = r[i];
-      }
-      tmem_st16(tG + cs + j0, g);
-    }
-    tmem_wait_st();
-    if (job.flags & 2) {
-      // the two halves' sums of this vector meet in the lower half
-      if (half) {
-        comb[0][vl] = P1;
-        comb[1][vl] = Rfb;
-      }
-      umma::fence_before_sync();
-      __syncthreads();
+      tmem_wait_st();
+      S64 += (double)Sacc;
+      Sacc = 0.f;
+    };
+    int jl = 0;
+    for (int jx = j_lo; jx < j_hi; ++jx, ++jl) {
+      const TcJob job = p.jobs[jx];
+      const TcTri tri = p.tris[job.tri];
+      const int b = tri.b, cs = job.cs, npad = job.npad;
+      const int buf = jl & 1;
+      float AQ = 1.f;
+      for (int j = 0; j < tri.nq; ++j) AQ *= atb[(size_t)tri.q[j] * p.Bpad];
+      const float mprime = (float)tri.mprime;
+      const float coef = AQ * mprime * inv_m;
+      if (!tc_wait(&bar_accf[buf], (uint32_t)(jl >> 1) & 1u, bad)) break;
       umma::fence_after_sync();
-      if (!half) {
-        P1 += comb[0][vl];
-        Rfb += comb[1][vl];
+      const uint32_t tR = tl + (uint32_t)buf * kTcAccCols;
+      for (int j0 = 0; j0 < npad; j0 += 16) {
+        float av[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int c = cs + j0 + i;
+          av[i] = (c > b && c < n) ? atb[(size_t)c * p.Bpad] : 0.f;
+        }
+        uint32_t ur[16], ug[16];
+        umma::tmem_ld16_async(tR + j0, ur);
+        umma::tmem_ld16_async(tG + cs + j0, ug);
+        umma::tmem_wait_ld();
+        float g[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const float r = __uint_as_float(ur[i]);
+          g[i] = __uint_as_float(ug[i]) + coef * r;
+          P1 += av[i] * r;
+          if (cs + j0 + i == b) Rfb = r;
+        }
+        tmem_st16(tG + cs + j0, g);
+      }
+      tmem_wait_st();
+      umma::fence_before_sync();
+      mbar_arrive(&bar_acce[buf]);  // this accumulator may take the job after next
+      if (job.flags & 2) {
         const float hb = b >= 0 ? ld_entry<ST>(p.K, tri.base) : 0.f;
         const float ab = b >= 0 ? atb[(size_t)b * p.Bpad] : 0.f;
         float T, Tr;
@@ -365,25 +336,80 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_batched_kernel(TcParams p) {
           tmem_st16(tG + l0, g);
           tmem_wait_st();
         }
+        P1 = 0.f;
+        Rfb = 0.f;
       }
-      P1 = 0.f;
-      Rfb = 0.f;
+      if (++since_flush == kTcFlushJobs) {
+        flush();
+        since_flush = 0;
+      }
     }
-    umma::fence_before_sync();
-    __syncthreads();  // the accumulator columns are read before the next job's MMAs overwrite them
-    if (++since_flush == kTcFlushJobs) {
-      flush();
-      since_flush = 0;
-      umma::fence_before_sync();
-      __syncthreads();  // both halves' flushes done before the lower half's next prefix updates
+    flush();
+    p.spart[(size_t)blockIdx.x * kTcSlice + vl] = S64;
+  } else if (w < kTcEpiWarps + kTcGatherWarps) {
+    // ---------------------------------------------------------------- gather
+    const int gt = tid - 32 * kTcEpiWarps;
+    uint32_t gc = 0;
+    for (int jx = j_lo; jx < j_hi; ++jx) {
+      const TcJob job = p.jobs[jx];
+      const TcTri tri = p.tris[job.tri];
+      bool ok = true;
+      for (int kc = job.kc0; kc < p.nkc; ++kc, ++gc) {
+        const int s = (int)(gc % kTcStages);
+        const uint32_t use = gc / kTcStages;
+        if (use > 0 && !tc_wait(&bar_empty[s], (use - 1) & 1u, bad)) {
+          ok = false;
+          break;
+        }
+        unsigned char *st = sm + s * kTcStageBytes;
+        if (gt == 0) {
+          mbar_expect_tx(&bar_afull[s], kTcAStage);
+          bulk_g2s(st, p.img + ((size_t)slice * p.nkc + kc) * (kTcAStage / 4), kTcAStage, &bar_afull[s]);
+        }
+        stage_rows<ST>(p, tri, job.cs, job.npad, 32 * kc, st + kTcAStage, st + kTcAStage + kTcBPart, gt);
+        fence_proxy_async();  // the rows written above become visible to the tensor cores
+        mbar_arrive(&bar_full[s]);
+      }
+      if (!ok) break;
+    }
+  } else if ((tid & 31) == 0) {
+    // ---------------------------------------------------------------- MMA issue
+    uint32_t gc = 0;
+    int jl = 0;
+    const uint32_t idesc_base = umma::idesc_tf32(kTcSlice, 16) & ~(0x3Fu << 17);
+    for (int jx = j_lo; jx < j_hi; ++jx, ++jl) {
+      const TcJob job = p.jobs[jx];
+      const int buf = jl & 1;
+      if (jl >= 2 && !tc_wait(&bar_acce[buf], (uint32_t)((jl >> 1) - 1) & 1u, bad)) break;
       umma::fence_after_sync();
+      const uint32_t tR = tbase + (uint32_t)buf * kTcAccCols;
+      const uint32_t idesc = idesc_base | ((uint32_t)(job.npad >> 3) << 17);
+      bool ok = true;
+      for (int kc = job.kc0; kc < p.nkc; ++kc, ++gc) {
+        const int s = (int)(gc % kTcStages);
+        const uint32_t par = (gc / kTcStages) & 1u;
+        if (!tc_wait(&bar_full[s], par, bad) || !tc_wait(&bar_afull[s], par, bad)) {
+          ok = false;
+          break;
+        }
+        umma::fence_after_sync();
+        const uint32_t a0 = saddr(sm + s * kTcStageBytes), b0 = a0 + kTcAStage;
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          const uint64_t ah = umma::desc_sw128(a0 + 32 * ks), al = umma::desc_sw128(a0 + kTcAPart + 32 * ks);
+          const uint64_t bh = umma::desc_sw128(b0 + 32 * ks), bl = umma::desc_sw128(b0 + kTcBPart + 32 * ks);
+          umma::mma_tf32(tR, ah, bh, idesc, (kc > job.kc0 || ks > 0) ? 1u : 0u);
+          umma::mma_tf32(tR, ah, bl, idesc, 1u);
+          umma::mma_tf32(tR, al, bh, idesc, 1u);
+        }
+        umma::mma_commit(&bar_empty[s]);
+      }
+      umma::mma_commit(&bar_accf[buf]);  // the epilogue may read this job's accumulator
+      if (!ok) break;
     }
-    if (s_bad) break;
+    // nothing may still write tensor memory when it is released
+    if (jl > 0) mbar_wait_bounded(&bar_accf[(jl - 1) & 1], (uint32_t)((jl - 1) >> 1) & 1u);
   }
-  flush();
-  if (!half) p.spart[(size_t)blockIdx.x * kTcSlice + vl] = S64;
-  // nothing may still write tensor memory when it is released
-  if (gchunk > 0) mbar_wait_bounded(&bar_mma[(gchunk - 1) & 1u], ((gchunk - 1) >> 1) & 1u);
   umma::fence_before_sync();
   __syncthreads();
   if (w == 0) umma::tmem_dealloc(tbase, 512);
@@ -613,8 +639,7 @@ int contract_batched_tc(const BatchedArgs &a, cudaStream_t st) {
   int slices = 0, P = 0;
   tc_shape(a.B, di.sms, &slices, &P);
   const int nkc = (n + 31) / 32, n16 = (n + 15) & ~15, Bpad = slices * kTcSlice, grid = slices * P;
-  const size_t smem = 1024 + 2 * (size_t)kTcAStage + 2 * (size_t)kTcBStage +
-                      (size_t)tc::kRowsPerJob * kTcSlice * sizeof(float);
+  const size_t smem = 1024 + (size_t)kTcStages * kTcStageBytes;
   if (smem > (size_t)di.smem_optin) return fail(TK_EUNSUPPORTED, "tensor-core batched kernel: shared memory");
   unsigned char *ws = reinterpret_cast<unsigned char *>(a.work);
   size_t njobs = 0, ntris = 0;

@@ -129,10 +129,9 @@ def tc_batched_rel(n: int, m: int) -> float:
       * each product of the 3-term TF32 split misses x*a by at most
         3.01 * 2^-22 |x a| (lo*lo' and the two residuals of the split), after
         one rounding of the weighted entry and one of the FP64 vector (2u);
-      * the hi*hi' accumulator sums n + 31 products, the cross-term one twice
-        as many 2^-10-smaller ones, each addition off by at most one FP32 ulp
-        (2u; no rounding mode of the tensor cores assumed), one more rounding
-        joins the two;
+      * one accumulator sums the 3 (n + 31) products of a row (hi*hi',
+        hi*lo', lo*hi' over at most n + 31 columns), each addition off by at
+        most one FP32 ulp (2u; no rounding mode of the tensor cores assumed);
       * the epilogue: A_Q (M'/m) with 2m - 3 roundings plus the product, at
         most 2 x 128 additions into the FP32 g accumulator between FP64
         flushes (one row and one prefix addition per job), the quadratic-form
@@ -143,7 +142,7 @@ def tc_batched_rel(n: int, m: int) -> float:
     in the a_b r_b correction)."""
     u = U32
     e_prod = 3.01 * 2.0 ** -22 + 2 * u
-    e_acc = 2 * u * (n + 31) * (1 + 2.0 ** -9) + u
+    e_acc = 2 * u * 3 * (n + 31)
     e_epi = u * ((2 * m - 2) + 2 * 128 + n + 12 + (m + 2))
     return e_prod + e_acc + e_epi
 
