@@ -107,6 +107,21 @@ int tk_row_align(int m, int64_t n, int64_t off, int64_t *row_off_host);
 int tk_build_packed(int m, int64_t n, int64_t d, const double *X, int feat,
                     int degree, int storage_dtype, void *K, void *stream);
 
+/* Which kernel builds FP32 / BF16 storage: 0 = the tensor-core build where it
+ * pays (d >= 64; tcgen05.mma kind::tf32 with the 3-term split), 1 = the
+ * tensor-core build for every FP32 / BF16 build, -1 = the SIMT build only.
+ * FP64 storage always takes the SIMT build.  Process-wide. */
+int tk_build_set_config(int tensor_cores);
+
+/* Status of the tensor-core builds issued so far on the current device:
+ * TK_ETIMEOUT if one of their bounded waits ran out (its entries are then not
+ * to be trusted), else TK_OK; reading clears it.  Synchronises `stream`. */
+int tk_build_status(void *stream);
+
+/* 1 if a build of d features into storage_dtype takes the tensor-core build
+ * under the current configuration on the current device, else 0. */
+int tk_build_path(int64_t d, int storage_dtype);
+
 /* Same for the offsets [off_lo, off_hi) only: K_range[o - off_lo] = K[o].
  * Lets a shard of the packed array be built on its own device. */
 int tk_build_packed_range(int m, int64_t n, int64_t d, const double *X, int feat,

@@ -94,6 +94,9 @@ def _declare(L):
         "tk_hessian": (i32, [i32, i64, i32, P, P, P, P, sz, P]),
         "tk_fma_probe": (i32, [i32, i32, ctypes.c_longlong, P, P]),
         "tk_umma_probe": (i32, [i32, i32, i32, P, P, P, P, sz, P]),
+        "tk_build_set_config": (i32, [i32]),
+        "tk_build_status": (i32, [P]),
+        "tk_build_path": (i32, [i64, i32]),
         "tk_primal": (i32, [i32, i64, i64, P, i64, P, P, P]),
         "tk_predict": (i32, [i64, i64, P, i64, P, P, P]),
         "tk_nystrom_select": (i32, [i64, i64, u64, P]),
@@ -296,6 +299,22 @@ def tk_umma_probe(A: torch.Tensor, B: torch.Tensor, split: bool = False, stream=
     if rc != TK_OK:
         raise TKError(rc, "the tensor-core probe's wait on its MMAs ran out")
     return D
+
+
+def tk_build_set_config(tensor_cores: int = 0) -> None:
+    """Which kernel builds FP32 / BF16 storage: 0 = tensor cores where they pay,
+    1 = always the tensor-core build, -1 = always the SIMT build."""
+    _check(lib().tk_build_set_config(int(tensor_cores)))
+
+
+def tk_build_uses_tensor_cores(d: int, storage="f32") -> bool:
+    """Whether a build of d features into `storage` takes the tensor-core build."""
+    return bool(lib().tk_build_path(int(d), dtype_code(storage)))
+
+
+def tk_build_status(stream=None) -> int:
+    """TK_ETIMEOUT if a tensor-core build's bounded wait ran out since the last read."""
+    return int(lib().tk_build_status(_stream(stream)))
 
 
 def tk_status_read(work: torch.Tensor, stream=None) -> int:

@@ -201,9 +201,29 @@ static int launch_build(const BParams &bp, cudaStream_t st) {
   return TK_OK;
 }
 
+int g_build_tc_mode = 0;
+
 }  // namespace tk
 
 using namespace tk;
+
+extern "C" int tk_build_set_config(int tensor_cores) {
+  if (tensor_cores < -1 || tensor_cores > 1) return fail(TK_EINVAL, "tensor_cores must be -1, 0 or 1");
+  g_build_tc_mode = tensor_cores;
+  return TK_OK;
+}
+
+extern "C" int tk_build_status(void *stream) { return build_tc_status(reinterpret_cast<cudaStream_t>(stream)); }
+
+static bool build_takes_tc(int64_t d, int storage) {
+  if (storage == TK_F64 || g_build_tc_mode < 0 || (g_build_tc_mode == 0 && d < 64)) return false;
+  int dev = 0, major = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess) return false;
+  return major == 10;
+}
+
+extern "C" int tk_build_path(int64_t d, int storage) { return build_takes_tc(d, storage) ? 1 : 0; }
 
 extern "C" int tk_build_packed_range(int m, int64_t n, int64_t d, const double *X, int feat, int degree,
                                      int storage, int64_t off_lo, int64_t off_hi, void *K, void *stream) {
@@ -240,6 +260,10 @@ extern "C" int tk_build_packed_range(int m, int64_t n, int64_t d, const double *
   }
   bp.total_tasks = total;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (build_takes_tc(d, storage)) {
+    const int rc = build_tc(m, (int)n, (int)d, X, feat, degree, storage, off_lo, off_hi, K, st);
+    if (rc != TK_EUNSUPPORTED) return rc;
+  }
   if (storage == TK_F64) return launch_build<double, double>(bp, st);
   if (storage == TK_F32) return launch_build<float, float>(bp, st);
   return launch_build<__nv_bfloat16, float>(bp, st);

@@ -100,6 +100,11 @@ int contract_batched(const BatchedArgs &a, cudaStream_t st);
 bool tc_covers(int m, int n, int storage, bool dual, int64_t B, int64_t off_lo, int64_t off_hi);
 size_t tc_workspace_bytes(int m, int n, int64_t B, int sms);
 int contract_batched_tc(const BatchedArgs &a, cudaStream_t st);
+// Tensor-core packed build (FP32 / BF16 storage) and its status flag.
+int build_tc(int m, int n, int d, const double *X, int feat, int degree, int storage, int64_t off_lo,
+             int64_t off_hi, void *K, cudaStream_t st);
+int build_tc_status(cudaStream_t st);
+extern int g_build_tc_mode;  // 0: where it pays, 1: always (FP32/BF16), -1: never
 extern tk_batched_config g_batched_cfg;
 // resolved batched launch shape; returns false when the kernel does not cover it
 bool batched_resolve(int n, int storage, bool dual, int64_t B, int sms, int smem_optin, tk_batched_config *out);

@@ -5,8 +5,8 @@ import torch
 
 import oracle
 import synth
-from gpu_util import U32, as_f64, batched_accumulation_depth, batched_bound, round_storage, tc_batched_bound, \
-    tc_batched_rel
+from gpu_util import U32, as_f64, batched_accumulation_depth, batched_bound, build_rel, round_storage, \
+    tc_batched_bound, tc_batched_rel
 
 pytestmark = pytest.mark.gpu
 
@@ -76,10 +76,14 @@ def test_batched_full_width_against_closed_form(path_tensor):
     A = synth.alpha_like(n, salt=830, batch=B)
     V = synth.alpha_like(n, salt=831, batch=B)
     Ad, Vd = torch.tensor(A, device="cuda"), torch.tensor(V, device="cuda")
-    cfg = tk.tk_batched_get_config(m, n, "f32", False, B)
-    assert cfg["vpl"] > 0  # the batched kernel serves this shape in one launch
-    G, S = tk.tk_contract(K, m, n, Ad)
-    HV, _ = tk.tk_contract(K, m, n, Ad, r=m - 2, V=Vd)
+    tk.tk_batched_set_config(tensor_cores=-1)  # the SIMT batched kernel (the tensor-core pass has its own test)
+    try:
+        cfg = tk.tk_batched_get_config(m, n, "f32", False, B)
+        assert cfg["vpl"] > 0 and cfg["tensor_cores"] == 0  # the SIMT kernel serves this shape in one launch
+        G, S = tk.tk_contract(K, m, n, Ad)
+        HV, _ = tk.tk_contract(K, m, n, Ad, r=m - 2, V=Vd)
+    finally:
+        tk.tk_batched_set_config(reset=True)
     G, S, HV = G.cpu().numpy(), S.cpu().numpy(), HV.cpu().numpy()
     U = A @ X                       # B x d: X^T a_b
     Ua = np.abs(A) @ np.abs(X)
@@ -88,9 +92,9 @@ def test_batched_full_width_against_closed_form(path_tensor):
     g_ref, g_abs = (U ** 3) @ X.T, (Ua ** 3) @ np.abs(X).T
     S_ref, S_abs = np.sum(U ** 4, axis=1), np.sum(Ua ** 4, axis=1)
     h_ref, h_abs = (U ** 2 * W) @ X.T, (Ua ** 2 * Wa) @ np.abs(X).T
-    kb = (d + m + 2)
-    rel = 1.01 * (kb + batched_accumulation_depth(n, m)) * U32
-    rel_h = 1.01 * (kb + batched_accumulation_depth(n, m, dual=True)) * U32
+    e_build = build_rel(d, m, "f32", tk.tk_build_uses_tensor_cores(d, "f32"))
+    rel = e_build + 1.01 * batched_accumulation_depth(n, m) * U32
+    rel_h = e_build + 1.01 * batched_accumulation_depth(n, m, dual=True) * U32
     assert np.all(np.abs(G - g_ref) <= rel * g_abs), float(np.max(np.abs(G - g_ref) / (rel * g_abs)))
     assert np.all(np.abs(S - S_ref) <= rel * S_abs)
     assert np.all(np.abs(HV - h_ref) <= rel_h * h_abs), float(np.max(np.abs(HV - h_ref) / (rel_h * h_abs)))
@@ -149,7 +153,7 @@ def test_tensor_core_full_width_against_closed_form(path_tensor, tensor_cores):
     U, Ua = A @ X, np.abs(A) @ np.abs(X)
     g_ref, g_abs = (U ** 3) @ X.T, (Ua ** 3) @ np.abs(X).T
     S_ref, S_abs = np.sum(U ** 4, axis=1), np.sum(Ua ** 4, axis=1)
-    rel = 1.01 * (d + m + 2) * U32 + 2.0 * tc_batched_rel(n, m)
+    rel = build_rel(d, m, "f32", tk.tk_build_uses_tensor_cores(d, "f32")) + 2.0 * tc_batched_rel(n, m)
     err = np.abs(G - g_ref) / g_abs
     print(f"\ntensor-core pass: max |err| / sum|terms| = {float(np.max(err)):.3e} (bound {rel:.3e})")
     assert np.all(np.abs(G - g_ref) <= rel * g_abs), float(np.max(np.abs(G - g_ref) / (rel * g_abs)))

@@ -8,7 +8,7 @@ import torch
 
 import oracle
 import synth
-from gpu_util import U32, UBF16, accumulation_depth, as_f64, max_warp_triangles
+from gpu_util import U32, UBF16, accumulation_depth, as_f64, build_rel, max_warp_triangles
 
 pytestmark = pytest.mark.gpu
 
@@ -47,7 +47,7 @@ def test_sampled_entries(built):
     for o, g in zip(offs, got):
         ref = oracle.build(X, m, int(o), int(o) + 1)[0]
         rabs = oracle.build(np.abs(X), m, int(o), int(o) + 1)[0]
-        tol = 1.01 * (d + m + 2) * U32 * rabs
+        tol = build_rel(d, m, storage, tk.tk_build_uses_tensor_cores(d, storage)) * rabs
         if storage == "bf16":
             tol += UBF16 * (abs(g) + tol)
         assert abs(g - ref) <= tol, (int(o), g, ref)
@@ -66,8 +66,10 @@ def test_contraction_closed_form(built):
         g_abs = np.abs(X) @ uabs ** (m - 1)
         S_abs = float(np.sum(uabs ** m))
         # storage rounding + build accumulation + contraction accumulation
-        k = (d + m + 2) + accumulation_depth(n, max_warp_triangles(m, n, storage))
-        rel = 1.01 * (U[storage] + k * U32) if storage == "bf16" else 1.01 * k * U32
+        rel = build_rel(d, m, storage, tk.tk_build_uses_tensor_cores(d, storage)) + \
+            1.01 * accumulation_depth(n, max_warp_triangles(m, n, storage)) * U32
+        if storage == "bf16":
+            rel += 1.01 * U[storage]
         err = np.abs(G.cpu().numpy() - g_ref)
         assert np.all(err <= rel * g_abs), float(np.max(err / (rel * g_abs)))
         assert abs(float(S[0]) - S_ref) <= rel * S_abs
@@ -84,8 +86,10 @@ def test_hvp_closed_form(built):
     hv_ref = X @ (u ** (m - 2) * (X.T @ v))
     uabs = np.abs(X).T @ np.abs(a)
     hv_abs = np.abs(X) @ (uabs ** (m - 2) * (np.abs(X).T @ np.abs(v)))
-    k = (d + m + 2) + 2 * accumulation_depth(n, max_warp_triangles(m, n, storage, dual=True))
-    rel = 1.01 * (U[storage] + k * U32) if storage == "bf16" else 1.01 * k * U32
+    rel = build_rel(d, m, storage, tk.tk_build_uses_tensor_cores(d, storage)) + \
+        1.01 * 2 * accumulation_depth(n, max_warp_triangles(m, n, storage, dual=True)) * U32
+    if storage == "bf16":
+        rel += 1.01 * U[storage]
     err = np.abs(HV.cpu().numpy() - hv_ref)
     assert np.all(err <= rel * hv_abs), float(np.max(err / (rel * hv_abs)))
 
@@ -102,7 +106,8 @@ def test_dexter_shaped_build_and_contraction():
     g_ref = X @ u ** (m - 1)
     uabs = np.abs(X).T @ np.abs(a)
     g_abs = np.abs(X) @ uabs ** (m - 1)
-    k = (d + m + 2) + accumulation_depth(n, max_warp_triangles(m, n, "f32"))
+    rel = build_rel(d, m, "f32", tk.tk_build_uses_tensor_cores(d, "f32")) + \
+        1.01 * accumulation_depth(n, max_warp_triangles(m, n, "f32")) * U32
     err = np.abs(G.cpu().numpy() - g_ref)
-    assert np.all(err <= 1.01 * k * U32 * g_abs + 1e-30), float(np.max(err / (1.01 * k * U32 * g_abs + 1e-30)))
-    assert abs(float(S[0]) - float(np.sum(u ** m))) <= 1.01 * k * U32 * float(np.sum(uabs ** m))
+    assert np.all(err <= rel * g_abs + 1e-30), float(np.max(err / (rel * g_abs + 1e-30)))
+    assert abs(float(S[0]) - float(np.sum(u ** m))) <= rel * float(np.sum(uabs ** m))
