@@ -107,10 +107,11 @@ int tk_row_align(int m, int64_t n, int64_t off, int64_t *row_off_host);
 int tk_build_packed(int m, int64_t n, int64_t d, const double *X, int feat,
                     int degree, int storage_dtype, void *K, void *stream);
 
-/* Which kernel builds FP32 / BF16 storage: 0 = the tensor-core build where it
- * pays (d >= 64; tcgen05.mma kind::tf32 with the 3-term split), 1 = the
- * tensor-core build for every FP32 / BF16 build, -1 = the SIMT build only.
- * FP64 storage always takes the SIMT build.  Process-wide. */
+/* Which kernel builds FP32 / BF16 storage: 0 (default) and -1 = the SIMT
+ * build, 1 = the tensor-core build (tcgen05.mma kind::tf32 with the 3-term
+ * split, a warp-specialised pipeline over 128 x 128 tiles of each triangle),
+ * which is correct but measured slower on GB300.  FP64 storage always takes
+ * the SIMT build.  Process-wide. */
 int tk_build_set_config(int tensor_cores);
 
 /* Status of the tensor-core builds issued so far on the current device:
