@@ -217,9 +217,8 @@ extern "C" int tk_build_status(void *stream) { return build_tc_status(reinterpre
 
 static bool build_takes_tc(int64_t d, int storage) {
   // the tensor-core build is opt-in: on GB300 it measured slower than the SIMT
-  // build (m = 4: n = 200, d = 20,000: 1096 vs 443 ms; n = 400, d = 100: 92 vs
-  // 29 ms), its fixed 128-row tile grid computing about 9x the entries of the
-  // many small triangles
+  // build (m = 4: n = 200, d = 20,000: 501 vs 443 ms; n = 400, d = 100: 56 vs
+  // 29 ms), bound by its operand-building warps rather than the tensor cores
   (void)d;
   if (storage == TK_F64 || g_build_tc_mode <= 0) return false;
   int dev = 0, major = 0;

@@ -6,13 +6,19 @@
 // matrix G^Q = X_{[b:n]} diag(w_Q) X_{[b:n]}^T, w_Q[k] = prod_{q in Q} x_{q,k},
 // passed through the feature map.
 //
-// GB300 mapping.  A task is one 128 x 128 tile (rows c, columns d >= c) of
-// one triangle on a fixed grid of 128-row tiles; tasks are enumerated per b
-// (multiset(b+1, m-3) triangles, each with T(nt - b/128) tile pairs) and
-// strided over a persistent grid of one block per SM.  The block is a
-// warp-specialised pipeline connected by mbarriers:
+// GB300 mapping.  The triangles with last value b (multiset(b+1, m-3) of them)
+// share their rows and columns [b, n), L = n - b.  A task is one MMA tile of
+// 128 rows: for L <= 128 the rows of floor(128/L) consecutive such triangles
+// stacked (columns [b, n)); for L > 128 one triangle's 128-row block c in
+// [b + 128 rt, ...) against the 128-column block d in [b + 128 ct, ...),
+// ct >= rt.  Tasks are enumerated per b and strided over a persistent grid of
+// one block per SM.  The block is a warp-specialised pipeline connected by
+// mbarriers:
 //   * warps 4-11 build, per 32-feature chunk, both operands from X in FP64 --
-//     A[c][k] = w_Q[k] x_{c,k} and B[d][k] = x_{d,k} -- round them to FP32,
+//     A[r][k] = x_{c_r,k} prod_{q in Q_r} x_{q,k} for row r's triangle Q_r and
+//     row c_r, B[j][k] = x_{d_j,k} -- with each triangle's weight row formed
+//     once per chunk (rounded to FP32), lanes along the features (coalesced
+//     loads, all of a warp's rows issued before use), round them to FP32,
 //     split them into TF32 hi and lo and store them in the K-major
 //     128-byte-swizzled layout of one of 3 ring stages;
 //   * one thread of warp 12 issues 4 k-steps of tcgen05.mma kind::tf32
@@ -20,9 +26,9 @@
 //     memory accumulator, hi.lo + lo.hi into a second (the large products
 //     summed apart from the small ones), two such pairs alternating between
 //     tasks;
-//   * warps 0-3 (thread i <-> tensor-memory lane i <-> row c0 + i) add the
-//     two accumulators, apply the feature map and write each row's entries
-//     d >= c to their packed offsets.
+//   * warps 0-3 (thread i <-> tensor-memory lane i <-> row i of the tile) add
+//     the two accumulators, apply the feature map and write row i's entries
+//     d >= c to its triangle's packed offsets.
 #include <cuda_bf16.h>
 
 #include "tk_umma.cuh"
@@ -41,7 +47,7 @@ constexpr int kCStageBytes = 4 * kCPart;  // A hi, A lo, B hi, B lo
 __device__ int g_tc_build_status;
 
 struct CParams {
-  int m, n, d, nt, nkc;
+  int m, n, d, nkc;
   const double *X;
   int feat, degree;
   void *K;  // entry off_lo
@@ -50,18 +56,26 @@ struct CParams {
 };
 
 struct CTask {
-  int b, bb, rt, ct;
-  int32_t q[kMaxOrder];
-  int64_t base;
-  bool live;
+  int b, L;          // last prefix value, rows/columns of its triangles
+  int stacked;       // 1: floor(128/L) whole triangles stacked, 0: one 128 x 128 block of one triangle
+  int64_t qi0;       // index (among the triangles with last value b) of the task's first triangle
+  int ntri;          // triangles in the task
+  int rt, ct;        // row / column block (L > 128)
+  int npad;          // columns, rounded up to 16 (N of the MMA)
 };
 
-__host__ __device__ __forceinline__ int64_t c_tiles(int nt, int b) {
-  const int k = nt - b / kCT;
-  return (int64_t)k * (k + 1) / 2;
+__host__ __device__ __forceinline__ int64_t c_count(int m, int n, int b) {
+  const int64_t cb = (m == 2) ? 1 : multiset(b + 1, m - 3);
+  const int L = n - b;
+  if (L <= kCT) {
+    const int k = kCT / L;
+    return (cb + k - 1) / k;
+  }
+  const int64_t lt = (L + kCT - 1) / kCT;
+  return cb * (lt * (lt + 1) / 2);
 }
 
-// Task t -> triangle (its prefix, b, packed base) and tile pair (rt, ct).
+// Task t -> its triangle group or block.
 __host__ __device__ __forceinline__ CTask c_decode(const CParams &p, const int64_t *pre, int64_t t) {
   CTask r;
   const int m = p.m, n = p.n;
@@ -73,20 +87,58 @@ __host__ __device__ __forceinline__ CTask c_decode(const CParams &p, const int64
     else hi = mid - 1;
   }
   const int b = (m == 2) ? 0 : lo;
-  const int rt0 = b / kCT, k = p.nt - rt0;
-  const int64_t T = (int64_t)k * (k + 1) / 2;
+  const int64_t cb = (m == 2) ? 1 : multiset(b + 1, m - 3);
+  const int L = n - b;
   const int64_t local = t - pre[lo];
-  const int64_t qi = local / T;
-  int tp = (int)(local - qi * T);
-  int rt = rt0;
-  while (tp >= p.nt - rt) {
-    tp -= p.nt - rt;
-    ++rt;
-  }
   r.b = b;
-  r.bb = b;
-  r.rt = rt;
-  r.ct = rt + tp;
+  r.L = L;
+  if (L <= kCT) {
+    const int k = kCT / L;
+    r.stacked = 1;
+    r.qi0 = local * k;
+    r.ntri = (int)(cb - r.qi0 < k ? cb - r.qi0 : k);
+    r.rt = r.ct = 0;
+    r.npad = (L + 15) & ~15;
+  } else {
+    const int lt = (L + kCT - 1) / kCT;
+    const int64_t T = (int64_t)lt * (lt + 1) / 2;
+    r.stacked = 0;
+    r.qi0 = local / T;
+    r.ntri = 1;
+    int tp = (int)(local - r.qi0 * T), rt = 0;
+    while (tp >= lt - rt) {
+      tp -= lt - rt;
+      ++rt;
+    }
+    r.rt = rt;
+    r.ct = rt + tp;
+    const int cols = min(kCT, L - kCT * r.ct);
+    r.npad = (cols + 15) & ~15;
+  }
+  return r;
+}
+
+// Row r of a task: its triangle (prefix Q, packed base of (Q, b, b)) and row c.
+struct CRow {
+  bool valid;
+  int c;
+  int32_t q[kMaxOrder];
+  int64_t base;
+};
+__host__ __device__ __forceinline__ CRow c_row(const CParams &p, const CTask &t, int r) {
+  CRow w;
+  const int m = p.m, n = p.n, b = t.b;
+  int64_t qi;
+  if (t.stacked) {
+    const int j = r / t.L;
+    w.valid = j < t.ntri;
+    qi = t.qi0 + (w.valid ? j : 0);
+    w.c = b + r - j * t.L;
+  } else {
+    w.c = b + kCT * t.rt + r;
+    w.valid = w.c < n;
+    qi = t.qi0;
+  }
   int32_t tup[kMaxOrder];
   if (m >= 3) {
     if (m > 3) unrank(m - 3, b + 1, qi, tup);
@@ -94,12 +146,12 @@ __host__ __device__ __forceinline__ CTask c_decode(const CParams &p, const int64
   }
   tup[m - 2] = b;
   tup[m - 1] = b;
-  for (int j = 0; j < m - 2; ++j) r.q[j] = tup[j];
-  r.base = (m == 2) ? 0 : rank(m, n, tup);
-  const int64_t L = n - b;
-  r.live = !(r.base + L * (L + 1) / 2 <= p.off_lo || r.base >= p.off_hi);
-  return r;
+  for (int j = 0; j < m - 2; ++j) w.q[j] = tup[j];
+  w.base = (m == 2) ? 0 : rank(m, n, tup);
+  return w;
 }
+
+__host__ __device__ __forceinline__ int c_col0(const CTask &t) { return t.b + (t.stacked ? 0 : kCT * t.ct); }
 
 template <typename ST>
 __device__ __forceinline__ void c_store(void *K, int64_t idx, float v);
@@ -129,25 +181,12 @@ __device__ __forceinline__ bool c_wait(uint64_t *bar, uint32_t parity, volatile 
   return false;
 }
 
-// 16 consecutive values of row `row` (features k0 .. k0+15 of X's row `xr`,
-// times w[0..15] when w is given) as TF32 hi/lo in the swizzled tile.
-__device__ __forceinline__ void c_row16(const CParams &p, int xr, bool valid, int k0, const double *w, int row, int kin,
-                                        unsigned char *thi, unsigned char *tlo) {
-  float h[16], l[16];
-  const double *xrow = p.X + (size_t)xr * p.d;
-#pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    const int k = k0 + i;
-    double x = (valid && k < p.d) ? xrow[k] : 0.0;
-    if (w) x *= w[i];
-    umma::split_tf32((float)x, h[i], l[i]);
-  }
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const uint32_t so = umma::sw128_offset((uint32_t)row, (uint32_t)(kin + 4 * j));
-    *reinterpret_cast<float4 *>(thi + so) = make_float4(h[4 * j], h[4 * j + 1], h[4 * j + 2], h[4 * j + 3]);
-    *reinterpret_cast<float4 *>(tlo + so) = make_float4(l[4 * j], l[4 * j + 1], l[4 * j + 2], l[4 * j + 3]);
-  }
+// Whether any entry of the task lies in [off_lo, off_hi).
+__host__ __device__ __forceinline__ bool c_live(const CParams &p, const CTask &t) {
+  const CRow f = c_row(p, t, 0);
+  const CRow l = c_row(p, t, t.stacked ? (t.ntri - 1) * t.L : 0);
+  const int64_t L = t.L;
+  return !(l.base + L * (L + 1) / 2 <= p.off_lo || f.base >= p.off_hi);
 }
 
 template <typename ST>
@@ -158,13 +197,14 @@ __global__ void __launch_bounds__(kCThreads, 1) tc_build_kernel(CParams p) {
   __shared__ int s_bad;
   unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(cb_smem_raw) + 1023) &
                                                         ~uintptr_t(1023));
-  int64_t *pre = reinterpret_cast<int64_t *>(sm + kCStages * kCStageBytes);      // [n + 1]
-  double *wbuf = reinterpret_cast<double *>(pre + (TK_MAX_POINTS + 1));          // [stages][32]
+  int64_t *pre = reinterpret_cast<int64_t *>(sm + kCStages * kCStageBytes);  // [n + 1]
+  float *wtab = reinterpret_cast<float *>(pre + (TK_MAX_POINTS + 1));        // [128 triangles][32 features]
+  int32_t *qtab = reinterpret_cast<int32_t *>(wtab + kCT * 32);               // [128 triangles][kMaxOrder]
+
   const int tid = threadIdx.x, w = tid >> 5;
   const int m = p.m, n = p.n;
   const int ngroups = (m == 2) ? 1 : n;
-  for (int b = tid; b < ngroups; b += blockDim.x)
-    pre[b + 1] = (m == 2 ? 1 : multiset(b + 1, m - 3)) * c_tiles(p.nt, b);
+  for (int b = tid; b < ngroups; b += blockDim.x) pre[b + 1] = c_count(m, n, b);
   if (w == 0) {
     umma::tmem_alloc(&tbase, 512);
     umma::tmem_relinquish();
@@ -197,21 +237,20 @@ __global__ void __launch_bounds__(kCThreads, 1) tc_build_kernel(CParams p) {
     int jl = 0;
     for (int64_t t = blockIdx.x; t < p.total_tasks; t += gridDim.x) {
       const CTask tsk = c_decode(p, pre, t);
-      if (!tsk.live) continue;
+      if (!c_live(p, tsk)) continue;
+      const CRow row = c_row(p, tsk, tid);
       const int buf = jl & 1;
       if (!c_wait(&bar_accf[buf], (uint32_t)(jl >> 1) & 1u, bad)) break;
       umma::fence_after_sync();
-      const int c = kCT * tsk.rt + tid, d0 = kCT * tsk.ct;
-      const int npad = min(kCT, ((n - d0) + 15) & ~15);
-      const bool row_ok = c >= tsk.bb && c < n;
-      const int64_t rowoff = tsk.base + (int64_t)(c - tsk.bb) * (2 * n - tsk.bb - c + 1) / 2 - c;
+      const int c = row.c, b = tsk.b, d0 = c_col0(tsk);
+      const int64_t rowoff = row.base + (int64_t)(c - b) * (2 * n - b - c + 1) / 2 - c;
       const uint32_t tb = tl + (uint32_t)buf * 256u, ts = tb + 128u;
-      for (int j0 = 0; j0 < npad; j0 += 16) {
+      for (int j0 = 0; j0 < tsk.npad; j0 += 16) {
         uint32_t ub[16], us[16];
         umma::tmem_ld16_async(tb + j0, ub);
         umma::tmem_ld16_async(ts + j0, us);
         umma::tmem_wait_ld();
-        if (!row_ok) continue;
+        if (!row.valid) continue;
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int dd = d0 + j0 + i;
@@ -228,35 +267,75 @@ __global__ void __launch_bounds__(kCThreads, 1) tc_build_kernel(CParams p) {
     }
   } else if (w < kCEpiWarps + kCGatherWarps) {
     // ---------------------------------------------------------------- operands
-    const int gt = tid - 32 * kCEpiWarps;
-    const int row = gt >> 1, kin = 16 * (gt & 1);
+    // per task the prefixes of its triangles go into a table; per chunk each
+    // triangle's weight row w_Q[k] = prod_{q in Q} x_{q,k} is formed once, then
+    // warp gw builds rows 16 gw .. 16 gw + 15 of both operands, lanes along
+    // the chunk's 32 features, all row loads issued before the first is used.
+    // (No early exit: the gathering warps meet at named barriers, so a wait
+    // that ran out only skips its stage and the loops run to the end.)
+    const int gt = tid - 32 * kCEpiWarps, gw = gt >> 5, lane = tid & 31;
     uint32_t gc = 0;
-    bool ok = true;
-    for (int64_t t = blockIdx.x; t < p.total_tasks && ok; t += gridDim.x) {
+    for (int64_t t = blockIdx.x; t < p.total_tasks; t += gridDim.x) {
       const CTask tsk = c_decode(p, pre, t);
-      if (!tsk.live) continue;
-      const int c = kCT * tsk.rt + row, dd = kCT * tsk.ct + row;
+      if (!c_live(p, tsk)) continue;
+      // the previous task's last chunk has been read by every gathering warp
+      asm volatile("bar.sync 1, %0;" ::"n"(kCGatherThreads) : "memory");
+      if (gt < tsk.ntri) {
+        const CRow first = c_row(p, tsk, tsk.stacked ? gt * tsk.L : 0);
+        for (int j = 0; j < m - 2; ++j) qtab[gt * kMaxOrder + j] = first.q[j];
+      }
+      int rc[16];
+      bool rv[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int r = 16 * gw + i;
+        if (tsk.stacked) {
+          const int j = r / tsk.L;
+          rv[i] = j < tsk.ntri;
+          rc[i] = tsk.b + r - j * tsk.L;
+        } else {
+          rc[i] = tsk.b + kCT * tsk.rt + r;
+          rv[i] = rc[i] < n;
+        }
+      }
+      const int d0 = c_col0(tsk);
       for (int kc = 0; kc < p.nkc; ++kc, ++gc) {
         const int s = (int)(gc % kCStages);
         const uint32_t use = gc / kCStages;
-        if (use > 0 && !c_wait(&bar_empty[s], (use - 1) & 1u, bad)) {
-          ok = false;
-          break;
+        const int k = 32 * kc + lane;
+        const bool kok = k < p.d;
+        // the weight rows of the task's triangles for this chunk
+        asm volatile("bar.sync 1, %0;" ::"n"(kCGatherThreads) : "memory");
+        for (int j = gw; j < tsk.ntri; j += kCGatherWarps) {
+          double wv = kok ? 1.0 : 0.0;
+          if (kok)
+            for (int jj = 0; jj < m - 2; ++jj) wv *= p.X[(size_t)qtab[j * kMaxOrder + jj] * p.d + k];
+          wtab[j * 32 + lane] = (float)wv;
         }
-        double *ws = wbuf + 32 * s;
-        if (gt < 32) {
-          const int k = 32 * kc + gt;
-          double wv = 0.0;
-          if (k < p.d) {
-            wv = 1.0;
-            for (int j = 0; j < m - 2; ++j) wv *= p.X[(size_t)tsk.q[j] * p.d + k];
-          }
-          ws[gt] = wv;
+        double xa[16], xb[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int r = 16 * gw + i, dd = d0 + r;
+          xa[i] = (rv[i] && kok) ? p.X[(size_t)rc[i] * p.d + k] : 0.0;
+          xb[i] = (r < tsk.npad && dd < n && kok) ? p.X[(size_t)dd * p.d + k] : 0.0;
         }
-        asm volatile("bar.sync 1, %0;" ::"n"(kCGatherThreads) : "memory");  // the chunk's weights are in place
+        asm volatile("bar.sync 1, %0;" ::"n"(kCGatherThreads) : "memory");  // weight rows in place
+        if (use > 0 && !c_wait(&bar_empty[s], (use - 1) & 1u, bad)) continue;
         unsigned char *st = sm + s * kCStageBytes;
-        c_row16(p, c, c < n, 32 * kc + kin, ws + kin, row, kin, st, st + kCPart);
-        c_row16(p, dd, dd < n, 32 * kc + kin, nullptr, row, kin, st + 2 * kCPart, st + 3 * kCPart);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int r = 16 * gw + i;
+          const int j = tsk.stacked ? r / tsk.L : 0;
+          const double a = rv[i] ? xa[i] * wtab[(j < tsk.ntri ? j : 0) * 32 + lane] : 0.0;
+          float h, l;
+          umma::split_tf32((float)a, h, l);
+          const uint32_t so = umma::sw128_offset((uint32_t)r, (uint32_t)lane);
+          *reinterpret_cast<float *>(st + so) = h;
+          *reinterpret_cast<float *>(st + kCPart + so) = l;
+          umma::split_tf32((float)xb[i], h, l);
+          *reinterpret_cast<float *>(st + 2 * kCPart + so) = h;
+          *reinterpret_cast<float *>(st + 3 * kCPart + so) = l;
+        }
         fence_proxy_async();  // the operands written above become visible to the tensor cores
         mbar_arrive(&bar_full[s]);
       }
@@ -269,13 +348,11 @@ __global__ void __launch_bounds__(kCThreads, 1) tc_build_kernel(CParams p) {
     bool ok = true;
     for (int64_t t = blockIdx.x; t < p.total_tasks && ok; t += gridDim.x) {
       const CTask tsk = c_decode(p, pre, t);
-      if (!tsk.live) continue;
+      if (!c_live(p, tsk)) continue;
       const int buf = jl & 1;
       if (jl >= 2 && !c_wait(&bar_acce[buf], (uint32_t)((jl >> 1) - 1) & 1u, bad)) break;
       umma::fence_after_sync();
-      const int d0 = kCT * tsk.ct;
-      const int npad = min(kCT, ((n - d0) + 15) & ~15);
-      const uint32_t idesc = idesc_base | ((uint32_t)(npad >> 3) << 17);
+      const uint32_t idesc = idesc_base | ((uint32_t)(tsk.npad >> 3) << 17);
       const uint32_t tb = tbase + (uint32_t)buf * 256u, ts = tb + 128u;
       for (int kc = 0; kc < p.nkc; ++kc, ++gc) {
         const int s = (int)(gc % kCStages);
@@ -310,7 +387,7 @@ __global__ void __launch_bounds__(kCThreads, 1) tc_build_kernel(CParams p) {
 
 size_t tc_build_smem() {
   return 1024 + (size_t)kCStages * kCStageBytes + (size_t)(TK_MAX_POINTS + 1) * sizeof(int64_t) +
-         (size_t)kCStages * 32 * sizeof(double);
+         (size_t)kCT * 32 * sizeof(float) + (size_t)kCT * kMaxOrder * sizeof(int32_t);
 }
 
 int build_tc(int m, int n, int d, const double *X, int feat, int degree, int storage, int64_t off_lo,
@@ -324,7 +401,6 @@ int build_tc(int m, int n, int d, const double *X, int feat, int degree, int sto
   p.m = m;
   p.n = n;
   p.d = d;
-  p.nt = (n + kCT - 1) / kCT;
   p.nkc = (d + 31) / 32;
   p.X = X;
   p.feat = feat;
@@ -333,10 +409,7 @@ int build_tc(int m, int n, int d, const double *X, int feat, int degree, int sto
   p.off_lo = off_lo;
   p.off_hi = off_hi;
   int64_t total = 0;
-  for (int b = 0; b < ((m == 2) ? 1 : n); ++b) {
-    const int k = p.nt - b / kCT;
-    total += (m == 2 ? 1 : multiset(b + 1, m - 3)) * ((int64_t)k * (k + 1) / 2);
-  }
+  for (int b = 0; b < ((m == 2) ? 1 : n); ++b) total += c_count(m, n, b);
   p.total_tasks = total;
   if (total == 0) return TK_OK;
   const int grid = (int)std::min<int64_t>(total, di.sms);

@@ -153,8 +153,8 @@ def tc_batched_bound(abs_terms: np.ndarray, n: int, m: int) -> np.ndarray:
 
 def tc_build_rel(d: int, m: int) -> float:
     """Relative bound (times sum_k prod_j |x|) of the tensor-core build of FP32
-    storage, from its arithmetic: an operand is w_Q x (or x) in FP64 rounded
-    once to FP32 (u each, 2u per product); the 3-term TF32 split misses a
+    storage, from its arithmetic: w_Q rounded to FP32 and w_Q x (or x) in
+    FP64 rounded to FP32 (3u per product); the 3-term TF32 split misses a
     product by at most 3.01 * 2^-22 of it; the hi*hi' accumulator sums at most
     d_pad = 32 ceil(d / 32) products, the cross-term one 2 d_pad products
     2^-10 smaller, each addition off by at most one FP32 ulp (2u: no rounding
@@ -162,7 +162,7 @@ def tc_build_rel(d: int, m: int) -> float:
     accumulators."""
     u = U32
     d_pad = 32 * ((d + 31) // 32)
-    return 2 * u + 3.01 * 2.0 ** -22 + 2 * u * d_pad + 2 * u * 2 * d_pad * 2.0 ** -10 * 1.001 + u
+    return 3 * u + 3.01 * 2.0 ** -22 + 2 * u * d_pad + 2 * u * 2 * d_pad * 2.0 ** -10 * 1.001 + u
 
 
 def build_rel(d: int, m: int, storage: str, tensor_cores: bool) -> float:
