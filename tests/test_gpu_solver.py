@@ -139,3 +139,35 @@ def test_relative_gap_stop():
     assert rc == tk.TK_OK and rep[0]["status"] == tk.TK_OK
     a_ref, info = oracle.solve_dual_newton(oracle.build(X, m), y, lam, m, tol=1e-12)
     assert abs(rep[0]["F"] - info["F"]) <= 1e-7 * max(1.0, abs(info["F"]))
+
+
+@pytest.mark.parametrize("method", ["newton_full", "newton_cg"])
+def test_batched_solve_through_tensor_cores(method):
+    # 72 problems (lambda in [0.3, 3]) at n = 96: the objective and gradient
+    # passes of the batch take the tensor-core batched contraction while at
+    # least 64 problems are active, then the SIMT kernels.  Every returned point
+    # is judged by its exact (FP64, closed-form) gradient, which bounds its
+    # distance to the exact minimiser (strong convexity); three problems are
+    # compared with the oracle's Newton minimiser.
+    m, n, d, B = 4, 96, 6, 72
+    X = synth.small_problem(m, n, d, salt=91, dist="uniform")
+    y = X @ synth.thesis_weights(synth.rng_for(5), d, 3) + 0.05 * synth.alpha_like(n, salt=92)
+    lams = np.geomspace(0.3, 3.0, B)
+    K = tk.tk_build_packed(torch.tensor(X, device="cuda"), m, storage="f32")
+    yt = torch.tensor(y, device="cuda")
+    tk.tk_batched_set_config(tensor_cores=1)
+    try:
+        assert tk.tk_batched_get_config(m, n, "f32", False, B)["tensor_cores"] == 1
+        A, rep, rc = tk.tk_solve_dual(K, m, n, yt, lams, method=method, tol=0.0, rel_gap=1e-9, max_iter=40,
+                                      K_hvp=K if method == "newton_full" else None)
+    finally:
+        tk.tk_batched_set_config(reset=True)
+    A = A.cpu().numpy()
+    for b in range(B):
+        ge = np.linalg.norm(_exact_grad(X, y, lams[b], m, A[b]))
+        assert ge <= 1e-4 * np.linalg.norm(y), (b, ge, rep[b])
+    Kx = oracle.build(X, m)
+    for b in (0, B // 2, B - 1):
+        a_ref, info = oracle.solve_dual_newton(Kx, y, lams[b], m, tol=1e-12)
+        ge = np.linalg.norm(_exact_grad(X, y, lams[b], m, A[b]))
+        assert np.linalg.norm(A[b] - a_ref) <= (ge + info["gradnorm"]) / lams[b] + 1e-12
