@@ -503,7 +503,10 @@ size_t tk_solve_workspace_size_opts(const tk_problem *P, const tk_solve_opts *O)
  *               from the previous accepted step.
  * A line search takes at most 10 trials (the cubic interpolation shrinks the
  * step 2-10-fold per trial); a problem whose step shrank 10^8-fold, or that
- * used its 10 trials without an accepted point, stops unconverged.
+ * used its 10 trials without an accepted point, stops unconverged.  So does a
+ * problem whose computed F falls below -|y|^2/(2 lambda) (kept points): K[a^m]
+ * >= 0 for an exact tensor of even order, so F cannot go lower, and a value
+ * below it shows that the stored tensor's rounding made its form negative.
  * Every objective is one contraction pass and every H v one dual-number pass
  * (tk_contract with r = m-2).  Writes one report per problem (host array of
  * B entries); returns TK_ENOTCONV if any problem missed tol (a problem also

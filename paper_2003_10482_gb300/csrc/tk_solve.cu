@@ -504,11 +504,36 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
     k_mask<<<grid_for(B * n), 256, 0, s.st>>>(B, n, P->mask, A);
     TK_CUDA_CHECK(cudaGetLastError());
   }
+  // The floor of F for an exact tensor of even order: K[a^m] >= 0, so
+  // F(a) >= (lambda/2)|a|^2 - <y, a> >= -|y|^2 / (2 lambda) over the kept
+  // points.  A computed F below it certifies that the stored tensor's form is
+  // negative at the point (its rounding has made it indefinite): the problem
+  // stops there, not at the end of a run-off along the null space of X^T.
+  std::vector<double> yk2(B), lam_b(B);
+  k_fill_y<<<grid_for(B * n), 256, 0, s.st>>>(B, n, P->y, s.w.at);
+  TK_CUDA_CHECK(cudaGetLastError());
+  if (P->mask) {
+    k_mask<<<grid_for(B * n), 256, 0, s.st>>>(B, n, P->mask, s.w.at);
+    TK_CUDA_CHECK(cudaGetLastError());
+  }
+  TK_TRY(s.dots(s.w.at, s.w.at, yk2));
+  TK_CUDA_CHECK(cudaMemcpyAsync(lam_b.data(), P->lambda, B * sizeof(double), cudaMemcpyDeviceToHost, s.st));
+  TK_CUDA_CHECK(cudaStreamSynchronize(s.st));
+  auto below_floor = [&](int64_t b, double Fv) {
+    return lam_b[b] > 0.0 && Fv < -(1.0 + 1e-9) * yk2[b] / (2.0 * lam_b[b]);
+  };
+
   TK_TRY(s.objective(A, s.w.F, s.w.g, s.w.gn2));
   for (auto &x : passes) ++x;
   TK_TRY(s.fetch(s.w.F, F));
   TK_TRY(s.fetch(s.w.gn2, gn2));
-  for (int64_t b = 0; b < B; ++b) best_gn2[b] = gn2[b];
+  for (int64_t b = 0; b < B; ++b) {
+    best_gn2[b] = gn2[b];
+    if (below_floor(b, F[b])) {
+      indefinite[b] = 1;
+      stalled[b] = 1;
+    }
+  }
 
   for (int it = 0; it < O->max_iter; ++it) {
     bool any = false;
@@ -647,6 +672,12 @@ extern "C" int tk_solve_dual(const tk_problem *P, const tk_solve_opts *O, double
       for (int64_t b = 0; b < B; ++b) {
         if (!ls[b]) continue;
         ++passes[b];
+        if (below_floor(b, Ft[b])) {  // the stored form is negative at the trial point
+          ls[b] = 0;
+          stalled[b] = 1;
+          indefinite[b] = 1;
+          continue;
+        }
         // Armijo sufficient decrease; once the decrease is below the rounding
         // level of F itself, a smaller gradient norm decides instead; a
         // non-positive slope at the trial point certifies decrease (F is
