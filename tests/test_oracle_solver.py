@@ -140,3 +140,29 @@ def test_dexter_shaped_generator():
     assert sup.size == 20 and np.all(np.any(X[:, sup] != 0.0, axis=0))
     assert np.all((np.abs(w[sup]) >= 0.7) & (np.abs(w[sup]) <= 1.0))
     assert np.allclose(p["y"], X @ w, atol=0.05 * 6)
+
+
+@pytest.mark.parametrize("m", [2, 4, 6])
+def test_dual_objective_floor(m):
+    # For an exact tensor of even order K[a^m] >= 0, so
+    # F(a) >= (lam/2)|a|^2 - <y, a> >= -|y|^2/(2 lam), with equality only at
+    # a = y/lam when K[(y/lam)^m] = 0 (y orthogonal to the features' span).
+    # The GPU solver stops a problem whose computed F goes below this floor.
+    n, d, lam = 9, 3, 0.37
+    X = synth.small_problem(m, n, d, salt=140 + m)
+    K = oracle.build(X, m)
+    rng = np.random.default_rng(141)
+    y = rng.standard_normal(n)
+    floor = -float(y @ y) / (2 * lam)
+    for _ in range(50):
+        a = rng.standard_normal(n) * rng.choice([1e-2, 1.0, 30.0])
+        _, S = oracle.contract(K, a, m)
+        assert S >= 0.0
+        assert oracle.dual_objective(S, a, y, lam, m) >= floor
+    # the floor is attained where the tensor vanishes: y in the null space of X^T
+    Q, _ = np.linalg.qr(X, mode="complete")
+    y0 = Q[:, d:] @ rng.standard_normal(n - d)  # X^T y0 = 0
+    a0 = y0 / lam
+    _, S0 = oracle.contract(K, a0, m)
+    assert abs(S0) <= 1e-12 * float(a0 @ a0) ** (m / 2) * np.abs(X).sum() ** m
+    assert oracle.dual_objective(S0, a0, y0, lam, m) == pytest.approx(-float(y0 @ y0) / (2 * lam), rel=1e-9)
