@@ -470,6 +470,61 @@ def dexter_leg(dev) -> dict:
     return out
 
 
+def methods_leg(dev) -> dict:
+    """Full-Hessian Newton against Newton-CG on the plain FP64 workload (m = 4,
+    n = 40, d = 10, lambda = 1e-2) to |grad F| <= 1e-10, and on the first stage
+    of the lambda path (the 64 problems with lambda in [0.41, 1], FP32 storage,
+    one batched call from the best multiple of y) to a 1e-7 relative gap:
+    passes over K, iterations and time of each method (CUDA-synchronised wall
+    clock, after a warm-up call)."""
+    import torch
+
+    import paper_2003_10482_gb300 as tk
+    import synth
+    out = {}
+    p = synth.plain_fp64()
+    m, X, y, lam = p["m"], p["X"], p["y"], p["lam"]
+    n = X.shape[0]
+    K = tk.tk_build_packed(torch.tensor(X, device=dev), m, storage="f64")
+    yt = torch.tensor(y, device=dev)
+    plain = {}
+    for method in ("newton_full", "newton_cg"):
+        tk.tk_solve_dual(K, m, n, yt, [lam], method=method, tol=1e-10, max_iter=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        A, rep, rc = tk.tk_solve_dual(K, m, n, yt, [lam], method=method, tol=1e-10, max_iter=100)
+        torch.cuda.synchronize()
+        plain[method] = {"seconds": time.perf_counter() - t0, "iterations": rep[0]["iters"],
+                         "passes": rep[0]["passes"], "gradnorm": rep[0]["gradnorm"], "status": rep[0]["status"]}
+    out["plain_fp64_m4_n40_d10"] = plain
+    bp = synth.batched_path()
+    idx = tk.tk_nystrom_select(bp["X"].shape[0], bp["n_prime"], bp["select_seed"])
+    Xb = torch.tensor(bp["X"][idx], device=dev)
+    yb = torch.tensor(bp["y"][idx], device=dev)
+    nb = Xb.shape[0]
+    lamb = torch.tensor(bp["lambdas"], device=dev)
+    maskb = torch.tensor(bp["masks"], device=dev)
+    js = list(range(8 * 56, 8 * 64))  # the 8 largest lambdas x 8 folds
+    K32 = tk.tk_build_packed(Xb, bp["m"], storage="f32")
+    stage = {}
+    for method in ("newton_full", "newton_cg"):
+        kw = {"K_hvp": K32, "start_on_y": True} if method == "newton_full" else {"start_on_y": True}
+        tk.tk_solve_dual(K32, bp["m"], nb, yb, lamb[js], mask=maskb[js], method=method, tol=0.0, rel_gap=1e-7,
+                         max_iter=1, **kw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        A, rep, rc = tk.tk_solve_dual(K32, bp["m"], nb, yb, lamb[js], mask=maskb[js], method=method, tol=0.0,
+                                      rel_gap=1e-7, max_iter=40, **kw)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        stage[method] = {"seconds": sec, "solves_per_s": len(js) / sec,
+                         "converged": sum(r["status"] == 0 for r in rep),
+                         "passes_total": sum(r["passes"] for r in rep), "passes_max": max(r["passes"] for r in rep),
+                         "iterations_max": max(r["iters"] for r in rep)}
+    out["lambda_path_stage0_fp32_64_problems"] = stage
+    return out
+
+
 def peaks_leg() -> dict:
     """Measured vector multiply-add rates (the denominators of the rooflines of
     the kernels bound by vector arithmetic)."""
@@ -624,6 +679,7 @@ def run_ours(args) -> None:
             line["peaks"] = peaks_leg()
             line["batched"] = batched_leg(dev)
             line["dexter_shaped"] = dexter_leg(dev)
+            line["methods"] = methods_leg(dev)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
