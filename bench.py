@@ -687,23 +687,39 @@ def run_ours(args) -> None:
 
 
 def run_case(args) -> None:
-    """One kernel a few times on the batched workload's tensor (m = 4, n' = 300
-    landmarks, FP32), for profiler captures: `hessian` runs tk_hessian,
-    `batched_pass` the B-vector contraction (tensor-core pass unless --tc -1).
-    Prints the mean CUDA-event time per call."""
+    """One kernel a few times, for profiler captures.  On the batched
+    workload's tensor (m = 4, n' = 300 landmarks, FP32): `hessian` runs
+    tk_hessian, `batched_pass` the B-vector contraction (tensor-core pass
+    unless --tc -1), `build` the packed build (SIMT unless --tc 1).  On the
+    first --n points of the full FP32 workload (m = 4, d = 100): `hvp` runs the
+    single-vector Hessian-vector pass.  Prints the mean CUDA-event time per call."""
     import torch
 
     import paper_2003_10482_gb300 as tk
     import synth
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    p = synth.batched_path()
-    m = p["m"]
-    idx = tk.tk_nystrom_select(p["X"].shape[0], p["n_prime"], p["select_seed"])
-    X = torch.tensor(p["X"][idx], device=dev)
-    n = X.shape[0]
+    if args.case == "hvp":
+        q = synth.full_fp32()
+        n = args.n if args.n > 0 else q["X"].shape[0]
+        X = torch.tensor(q["X"][:n], device=dev)
+        m = q["m"]
+    else:
+        p = synth.batched_path()
+        m = p["m"]
+        idx = tk.tk_nystrom_select(p["X"].shape[0], p["n_prime"], p["select_seed"])
+        X = torch.tensor(p["X"][idx], device=dev)
+        n = X.shape[0]
+    if args.case == "build":
+        tk.tk_build_set_config(1 if args.build_tc else -1)
     K = tk.tk_build_packed(X, m, storage="f32")
-    if args.case == "hessian":
+    if args.case == "build":
+        call = lambda: tk.tk_build_packed(X, m, storage="f32", K=K)  # noqa: E731
+    elif args.case == "hvp":
+        a = torch.tensor(synth.alpha_like(n, salt=7), device=dev)
+        v = torch.tensor(synth.alpha_like(n, salt=8), device=dev)
+        call = lambda: tk.tk_contract(K, m, n, a, r=m - 2, V=v)  # noqa: E731
+    elif args.case == "hessian":
         a = torch.tensor(synth.alpha_like(n, salt=3), device=dev)
         call = lambda: tk.tk_hessian(K, m, n, a)  # noqa: E731
     else:
@@ -733,8 +749,9 @@ def main():
                     help="skip the batched-vs-FP64 dual-solve comparison")
     ap.add_argument("--n", type=int, default=0,
                     help="points of the workload (default: all 400); smaller n for profiler captures")
-    ap.add_argument("--case", choices=["hessian", "batched_pass"], default=None,
-                    help="run one kernel on the batched workload's tensor (profiler captures) and exit")
+    ap.add_argument("--case", choices=["hessian", "batched_pass", "build", "hvp"], default=None,
+                    help="run one kernel a few times (profiler captures) and exit")
+    ap.add_argument("--build-tc", action="store_true", help="--case build: the tensor-core build")
     ap.add_argument("--B", type=int, default=128, help="vectors of --case batched_pass")
     ap.add_argument("--tc", type=int, default=1, choices=[1, -1], help="--case batched_pass: tensor cores or SIMT")
     args = ap.parse_args()
