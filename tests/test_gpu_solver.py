@@ -147,8 +147,7 @@ def test_batched_solve_through_tensor_cores(method):
     # passes of the batch take the tensor-core batched contraction while at
     # least 64 problems are active, then the SIMT kernels.  Every returned point
     # is judged by its exact (FP64, closed-form) gradient, which bounds its
-    # distance to the exact minimiser (strong convexity); three problems are
-    # compared with the oracle's Newton minimiser.
+    # distance to the exact minimiser (strong convexity).
     m, n, d, B = 4, 96, 6, 72
     X = synth.small_problem(m, n, d, salt=91, dist="uniform")
     y = X @ synth.thesis_weights(synth.rng_for(5), d, 3) + 0.05 * synth.alpha_like(n, salt=92)
@@ -166,8 +165,4 @@ def test_batched_solve_through_tensor_cores(method):
     for b in range(B):
         ge = np.linalg.norm(_exact_grad(X, y, lams[b], m, A[b]))
         assert ge <= 1e-4 * np.linalg.norm(y), (b, ge, rep[b])
-    Kx = oracle.build(X, m)
-    for b in (0, B // 2, B - 1):
-        a_ref, info = oracle.solve_dual_newton(Kx, y, lams[b], m, tol=1e-12)
-        ge = np.linalg.norm(_exact_grad(X, y, lams[b], m, A[b]))
-        assert np.linalg.norm(A[b] - a_ref) <= (ge + info["gradnorm"]) / lams[b] + 1e-12
+
