@@ -10,29 +10,31 @@
 //   R (vectors x rows) = A (vectors x d) . S~_Q^T (d x rows),
 // and an epilogue turns R into the g and S contributions.
 //
-// GB300 mapping.  A block (128 threads, one per SM: it holds all 512 columns
+// GB300 mapping.  A block (416 threads, one per SM: it holds all 512 columns
 // of tensor memory) owns a slice of 128 vectors -- tensor-memory lane i is
 // vector i of the slice -- and a contiguous range of jobs; a job is up to 96
-// rows of one triangle (rows c in [cs, cs + 96), cs a multiple of 16).  For
-// every 32-wide chunk of the column index d the job:
-//   * copies the slice's vectors for that chunk, pre-split into TF32 hi and
-//     lo parts and pre-swizzled (a 32 KB image written once per pass), into
-//     one of two stages with one cp.async.bulk (mbarrier completion);
-//   * gathers the chunk of S~_Q's rows from the packed triangle -- entry
+// rows of one triangle (rows c in [cs, cs + 96), cs a multiple of 16).  The
+// block is a warp-specialised pipeline connected by mbarriers:
+//   * warps 4-11 walk the jobs chunk by 32-wide chunk of the column index d:
+//     they gather the chunk of S~_Q's rows from the packed triangle -- entry
 //     (c, d) from row min(c, d), lanes running along whichever index is
-//     contiguous in memory -- weights column b, splits it into TF32 hi/lo and
-//     stores both in the K-major 128-byte-swizzled layout;
-//   * one thread issues 4 k-steps x 3 tcgen05.mma (hi.hi into one
-//     accumulator, hi.lo + lo.hi into a second, so that the large products
-//     are summed apart from the small ones; M = 128 vectors, N = the job's
-//     rows, K = 8) and commits them to the stage's mbarrier, so the next
-//     chunk is gathered while these run.
-// The epilogue reads the accumulator (tcgen05.ld), adds A_Q (M'/m) Rf_c into
-// the block's g accumulator -- 128 x n FP32 values in tensor memory, column
-// c -- and carries the triangle's quadratic-form sum; the triangle's last job
-// adds its S and prefix-value terms.  Every few hundred jobs the g
-// accumulator is added into the block's FP64 partial (bounded FP32
-// summation depth); a second kernel sums the partials in a fixed order.
+//     contiguous in memory -- weight column b, split it into TF32 hi/lo and
+//     store both in the K-major 128-byte-swizzled layout of one of 3 ring
+//     stages; their first thread also starts the cp.async.bulk of the slice's
+//     vectors for the chunk (pre-split into TF32 hi and lo and pre-swizzled:
+//     a 32 KB image written once per pass) into the same stage;
+//   * one thread of warp 12 waits for a stage, issues 4 k-steps x 3
+//     tcgen05.mma (hi.hi + hi.lo + lo.hi; M = 128 vectors, N = the job's
+//     rows, K = 8) into one of two alternating job accumulators and commits
+//     the stage back to the gatherers, and the accumulator to the epilogue at
+//     the job's end;
+//   * warps 0-3 read the accumulator (tcgen05.ld), hand it back, add
+//     A_Q (M'/m) Rf_c into the block's g accumulator -- 128 x n FP32 values in
+//     tensor memory, column c, each thread its own lane -- and carry the
+//     triangle's quadratic-form sum; the triangle's last job adds its S and
+//     prefix-value terms.  Every 128 jobs the g accumulator is added into the
+//     block's FP64 partial (bounded FP32 summation depth); a second kernel
+//     sums the partials in a fixed order.
 #include <cuda_bf16.h>
 #include <string.h>
 
