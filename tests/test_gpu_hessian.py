@@ -94,6 +94,8 @@ def test_full_newton_low_precision(storage):
     a = A[0].cpu().numpy()
     u = X.T @ a
     ge = np.linalg.norm(X @ u ** (m - 1) + lam * a - y)
-    a_ref, info = oracle.solve_dual_newton(oracle.build(X, m), y, lam, m, tol=1e-12)
+    # the oracle stops at its own rounding floor (about 3e-8 here, reached in 7
+    # iterations); the bound uses the gradient norm it reached
+    a_ref, info = oracle.solve_dual_newton(oracle.build(X, m), y, lam, m, tol=1e-12, max_iter=15)
     assert np.linalg.norm(a - a_ref) <= ge / lam + info["gradnorm"] / lam + 1e-12
     assert ge <= (1e-4 if storage == "f32" else 3e-2) * np.linalg.norm(y)
