@@ -201,7 +201,6 @@ static int resolve(int m, int n, int storage, bool dual, Resolved *r) {
   DevInfo di;
   int rc = dev_info(&di);
   if (rc != TK_OK) return rc;
-  (void)m;
   const int es = dtype_size(storage);
   const int cts = storage == TK_F64 ? 8 : 4;
   r->nc = pick_nc(n);
@@ -238,8 +237,15 @@ static int resolve(int m, int n, int storage, bool dual, Resolved *r) {
   r->warp_bytes = (fixed + gbytes + r->nbuf * r->buf_bytes + 127) & ~127;
   r->grid = di.sms * r->cps;
   r->smem = (size_t)r->vec_bytes + (size_t)warps * r->warp_bytes;
-  r->row_cost = o.row_cost > 0 ? o.row_cost : 256;
-  r->tri_cost = o.tri_cost > 0 ? o.tri_cost : 4 * r->row_cost;
+  // cost weights of the work cut: the dual (HVP) pass, BF16 storage and the
+  // many small triangles of m >= 5 balance best with cheap rows and dear
+  // triangles (measured on GB300 by the launch-configuration sweep: HVP m = 4,
+  // n = 400 FP32 3.48 -> 3.80 TB/s; BF16 n = 600 3.70 -> 3.84 TB/s and its HVP
+  // 2.40 -> 2.59 TB/s; m = 6, n = 80 0.60 -> 0.66 TB/s); the single FP32/FP64
+  // pass at m <= 4 keeps 256 / 1024
+  const bool cheap_rows = dual || storage == TK_BF16 || m >= 5;
+  r->row_cost = o.row_cost > 0 ? o.row_cost : (cheap_rows ? 64 : 256);
+  r->tri_cost = o.tri_cost > 0 ? o.tri_cost : (cheap_rows ? 4096 : 4 * r->row_cost);
   r->ppw = o.pieces_per_warp > 0 ? o.pieces_per_warp : 16;
   if (r->ppw > kMaxPiecesPerWarp) return fail(TK_EINVAL, "pieces_per_warp above %d", kMaxPiecesPerWarp);
   r->schedule = o.schedule > 0 ? o.schedule : 1;
