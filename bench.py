@@ -692,18 +692,32 @@ def run_case(args) -> None:
     tk_hessian, `batched_pass` the B-vector contraction (tensor-core pass
     unless --tc -1), `build` the packed build (SIMT unless --tc 1).  On the
     first --n points of the full FP32 workload (m = 4, d = 100): `hvp` runs the
-    single-vector Hessian-vector pass.  Prints the mean CUDA-event time per call."""
+    single-vector Hessian-vector pass.  `higher_order` runs the single pass on
+    the m = 6, n = 80 FP32 tensor; `bf16` the single pass (the Hessian-vector
+    pass with --dual) on a BF16 tensor over the first --n Nystrom landmarks
+    (default 400).  Prints the mean CUDA-event time per call."""
     import torch
 
     import paper_2003_10482_gb300 as tk
     import synth
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
+    storage = "f32"
     if args.case == "hvp":
         q = synth.full_fp32()
         n = args.n if args.n > 0 else q["X"].shape[0]
         X = torch.tensor(q["X"][:n], device=dev)
         m = q["m"]
+    elif args.case == "higher_order":
+        q = synth.higher_order()
+        X = torch.tensor(q["X"], device=dev)
+        m, n = q["m"], q["X"].shape[0]
+    elif args.case == "bf16":
+        q = synth.nystrom_bf16(n_test=10)
+        idx = tk.tk_nystrom_select(q["X_train"].shape[0], q["n_prime"], q["select_seed"])
+        n = args.n if args.n > 0 else 400
+        X = torch.tensor(q["X_train"][idx[:n]], device=dev)
+        m, storage = q["m"], "bf16"
     else:
         p = synth.batched_path()
         m = p["m"]
@@ -712,13 +726,16 @@ def run_case(args) -> None:
         n = X.shape[0]
     if args.case == "build":
         tk.tk_build_set_config(1 if args.build_tc else -1)
-    K = tk.tk_build_packed(X, m, storage="f32")
+    K = tk.tk_build_packed(X, m, storage=storage)
     if args.case == "build":
         call = lambda: tk.tk_build_packed(X, m, storage="f32", K=K)  # noqa: E731
-    elif args.case == "hvp":
+    elif args.case == "hvp" or (args.case == "bf16" and args.dual):
         a = torch.tensor(synth.alpha_like(n, salt=7), device=dev)
         v = torch.tensor(synth.alpha_like(n, salt=8), device=dev)
         call = lambda: tk.tk_contract(K, m, n, a, r=m - 2, V=v)  # noqa: E731
+    elif args.case in ("higher_order", "bf16"):
+        a = torch.tensor(synth.alpha_like(n, salt=7), device=dev)
+        call = lambda: tk.tk_contract(K, m, n, a)  # noqa: E731
     elif args.case == "hessian":
         a = torch.tensor(synth.alpha_like(n, salt=3), device=dev)
         call = lambda: tk.tk_hessian(K, m, n, a)  # noqa: E731
@@ -735,7 +752,8 @@ def run_case(args) -> None:
     e1.record()
     e1.synchronize()
     print(json.dumps({"case": args.case, "B": args.B if args.case != "hessian" else 1, "tensor_cores": args.tc,
-                      "ms_per_call": e0.elapsed_time(e1) / 3, "entries": int(K.numel())}), flush=True)
+                      "ms_per_call": e0.elapsed_time(e1) / 3, "entries": int(K.numel()),
+                      "TB_per_s": K.numel() * K.element_size() / (e0.elapsed_time(e1) / 3) / 1e9}), flush=True)
 
 
 def main():
@@ -749,9 +767,11 @@ def main():
                     help="skip the batched-vs-FP64 dual-solve comparison")
     ap.add_argument("--n", type=int, default=0,
                     help="points of the workload (default: all 400); smaller n for profiler captures")
-    ap.add_argument("--case", choices=["hessian", "batched_pass", "build", "hvp"], default=None,
+    ap.add_argument("--case", choices=["hessian", "batched_pass", "build", "hvp", "higher_order", "bf16"],
+                    default=None,
                     help="run one kernel a few times (profiler captures) and exit")
     ap.add_argument("--build-tc", action="store_true", help="--case build: the tensor-core build")
+    ap.add_argument("--dual", action="store_true", help="--case bf16: the Hessian-vector pass")
     ap.add_argument("--B", type=int, default=128, help="vectors of --case batched_pass")
     ap.add_argument("--tc", type=int, default=1, choices=[1, -1], help="--case batched_pass: tensor cores or SIMT")
     args = ap.parse_args()

@@ -12,7 +12,15 @@ by the reference's.  BF16 storage alone makes the stored quartic form
 indefinite along the null space of X^T (600 landmarks > 200 features), so its
 own minimiser runs off; the mixed scheme reads the BF16 copy only in the
 Hessian-vector passes and the FP32 tensor for the objective and gradient,
-whose zero defines the solution."""
+whose zero defines the solution.
+
+The test MSE is not bounded usefully by the objective gap: lambda-strong
+convexity alone lets |a - a_ref| reach (|grad F(a)| + |grad F(a_ref)|) / lambda,
+and that worst case moves the predictions by orders of magnitude more than the
+MSE itself.  The two models are therefore required to agree within the
+sampling error of the test MSE (the standard error of the mean squared
+residual over the 10,000 held-out points), the resolution at which the
+test MSE of Section 6.1 measures anything."""
 import time
 
 import numpy as np
@@ -84,32 +92,17 @@ def test_nystrom_solution_matches_fp64(nystrom, scheme):
     assert abs(F - F_ref) <= REL_TARGET * abs(F_ref)
     true_sup = set(np.flatnonzero(nys["c"]["w_true"]).tolist())
     assert sup == sup_ref and true_sup <= sup_ref  # the 2 std threshold finds all of w*'s support
-    dmse = _mse_bound(nys, nys["A64"][0], g, g_ref, lam, mse_ref)
-    print(f"|MSE - MSE_ref| = {abs(mse - mse_ref):.3e} <= {dmse:.3e}")
-    assert abs(mse - mse_ref) <= dmse
+    # the two models differ by less than the sampling error of the test MSE
+    # itself: the standard error of the mean of the N_test squared residuals
+    se = _mse_standard_error(nys, nys["A64"][0])
+    print(f"|MSE - MSE_ref| = {abs(mse - mse_ref):.3e} <= SE {se:.3e}")
+    assert abs(mse - mse_ref) <= se
 
 
-def _mse_bound(nys, a_ref, g, g_ref, lam, mse_ref):
-    """Bound on |MSE(a) - MSE(a_ref)| from the two exact gradient norms.
-
-    F is lambda-strongly convex, so |a - a*| <= |grad F(a)| / lambda for any a
-    and |a - a_ref| <= D = (g + g_ref) / lambda.  With u = X_L^T a, column j
-    of X_L moves u_j by at most c_j D (c_j its 2-norm).  The representer map
-    w_j = sign(u_j) |u_j|^{m-1} has derivative (m-1) |u_j|^{m-2}, so by the mean
-    value theorem |dw_j| <= (m-1) (|u_ref,j| + c_j D)^{m-2} c_j D = b_j, and
-    the test predictions move by |delta| <= sigma_max(X_test) |b|.  With
-    r_ref the reference residuals, MSE - MSE_ref = (2 <r_ref, delta> + |delta|^2)
-    / N_test, bounded by Cauchy-Schwarz; 1e-12 MSE_ref covers the rounding of
-    the FP64 predictions."""
-    m = nys["m"]
-    XL = nys["XL"].double().cpu().numpy()
-    Xt = nys["Xt"].double().cpu().numpy()
-    y_test = np.asarray(nys["c"]["y_test"], dtype=np.float64).reshape(-1)
-    u_ref = XL.T @ a_ref.double().cpu().numpy()
-    D = (g + g_ref) / lam
-    c = np.linalg.norm(XL, axis=0)
-    b = (m - 1) * (np.abs(u_ref) + c * D) ** (m - 2) * c * D
-    delta = np.linalg.norm(Xt, 2) * np.linalg.norm(b)
-    N = Xt.shape[0]
-    r_ref = np.sqrt(mse_ref * N)  # |r_ref|_2
-    return (2 * r_ref * delta + delta * delta) / N + 1e-12 * mse_ref
+def _mse_standard_error(nys, a):
+    """Standard error of the test MSE of solution a: std of the squared
+    residuals over sqrt(N_test)."""
+    W = tk.tk_primal(nys["XL"], a, nys["m"])
+    yhat = tk.tk_predict(nys["Xt"], W).cpu().numpy().reshape(-1)
+    sq = (yhat - np.asarray(nys["c"]["y_test"], dtype=np.float64).reshape(-1)) ** 2
+    return float(np.std(sq, ddof=1) / np.sqrt(sq.size))
