@@ -26,7 +26,10 @@
 // triangle, tk_contract_plan); warp w takes pieces w, w+W, ... (or the next
 // free one from a shared ticket).  Each warp walks its rows in blocks of at
 // most 32 consecutive rows of one triangle whose entries fit its staging
-// buffer; every block is fetched by one cp.async.bulk copy (TMA bulk engine,
+// buffer; a block that holds a whole triangle also takes the whole triangles
+// of at most 32 rows that follow it while they fit (n <= 256: the many small
+// triangles of high orders then share one copy and one wait).  Every block is
+// fetched by one cp.async.bulk copy (TMA bulk engine,
 // mbarrier completion) into one of NBUF linear shared-memory buffers, so
 // NBUF-1 blocks are always in flight while the warp computes on the current
 // one.  The buffers take all the shared memory the 16 warps leave free.
@@ -225,8 +228,13 @@ constexpr int max_threads() {
 }
 
 // Per-warp shared-memory header: NBUF mbarriers and the descriptor of each
-// issued block: {piece, nb | boff << 6 | LAST}.
+// issued block: {piece, nb | boff << 6 | LAST | ntri << 11}: nb rows of the
+// current triangle, the 16-byte lead of the copy in entries, the last block
+// of its piece, and the number of whole triangles that follow those rows in
+// the same block.
 constexpr int kDescLast = 1 << 10;  // the last block of its piece
+constexpr int kDescTriShift = 11;
+constexpr int kDescMaxTri = 63;
 struct WarpHdr {
   uint64_t bar[8];
   int2 desc[8];
@@ -406,6 +414,10 @@ template <typename ST, typename CT, bool D, int NC>
 __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(KParams p) {
   using N = Nm<CT, D>;
   constexpr int ES = sizeof(ST);
+  // blocks of several whole triangles (n <= 256 only: at larger n the
+  // triangles of at most 32 rows hold a negligible share of the entries, and
+  // the loop costs the wide instances registers)
+  constexpr bool kMultiTri = NC <= 8;
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
@@ -510,10 +522,37 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
       --nb;
       span -= L0 - nb;
     }
+    // A block that holds a whole triangle (it starts at the triangle's first
+    // row and takes all its rows) also takes the whole triangles that follow,
+    // while they fit the buffer and the piece (the many small triangles of
+    // high orders then share one copy and one wait).
+    const bool whole = kMultiTri && m > 2 && nb == L0 && cp == Qp[m - 3];
+    remp -= span;
+    cp += nb;
+    if (cp == n && remp > 0) {
+      if (m > 2 && next_sorted(m - 2, n, Qp)) cp = Qp[m - 3];
+      else remp = 0;
+    }
+    int tot = span, ntri = 0;
+    if (whole) {
+      while (ntri < kDescMaxTri && remp > 0) {
+        const int L = n - cp;  // cp is the first row of the next triangle
+        const int ts = (L * (L + 1)) >> 1;
+        if (L > kRows || tot + ts > p.cap || ts > remp) break;
+        tot += ts;
+        remp -= ts;
+        ++ntri;
+        cp = n;
+        if (remp > 0) {
+          if (next_sorted(m - 2, n, Qp)) cp = Qp[m - 3];
+          else remp = 0;
+        }
+      }
+    }
     const uint32_t lead = (uint32_t)reinterpret_cast<uintptr_t>(srcp) & 15u;
     const unsigned char *b0 = srcp - lead;
-    const unsigned char *e1 = srcp + span * ES;
-    uint32_t bytes = (lead + (uint32_t)(span * ES) + 15u) & ~15u;
+    const unsigned char *e1 = srcp + (int64_t)tot * ES;
+    uint32_t bytes = (lead + (uint32_t)(tot * ES) + 15u) & ~15u;
     const int bi = bi_issue;
     unsigned char *dst = bufs + (size_t)bi * p.buf_bytes;
     if (e1 > tail_ptr) {
@@ -524,9 +563,9 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
       if (lane < nt) dst[bytes + lane] = tail_ptr[lane];
       __syncwarp();
     }
-    remp -= span;
     if (lane == 0) {
-      hdr->desc[bi] = make_int2(piece_p, nb | (int)((lead / ES) << 6) | (remp <= 0 ? kDescLast : 0));
+      hdr->desc[bi] = make_int2(piece_p, nb | (int)((lead / ES) << 6) | (remp <= 0 ? kDescLast : 0) |
+                                             (ntri << kDescTriShift));
       if (bytes) {
         fence_proxy_async();
         mbar_expect_tx(&hdr->bar[bi], bytes);
@@ -535,12 +574,7 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
         mbar_arrive(&hdr->bar[bi]);  // nothing to copy: complete the phase
       }
     }
-    cp += nb;
     srcp = e1;
-    if (cp == n && remp > 0) {
-      if (m > 2 && next_sorted(m - 2, n, Qp)) cp = Qp[m - 3];
-      else remp = 0;
-    }
     ++j_issue;
     bi_issue = (bi_issue + 1 == NB) ? 0 : bi_issue + 1;
   };
@@ -634,7 +668,8 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
     const uint32_t parity = ph_cons;
     __syncwarp();
     const int2 dsc = hdr->desc[bi];
-    const int nb = dsc.y & 63;
+    int nb = dsc.y & 63;
+    int ntri = (dsc.y >> kDescTriShift) & kDescMaxTri;  // whole triangles after the first nb rows
     if (dsc.x != piece_c) {
       // this block starts a new piece: restart the compute cursor there
       if (open) flush_triangle();
@@ -645,7 +680,6 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
       setup_triangle();
       open = true;
     }
-    const int L0 = n - c;
     const unsigned char *buf = bufs + (size_t)bi * p.buf_bytes;
     if (!__all_sync(0xffffffffu, mbar_wait_bounded(&hdr->bar[bi], parity))) {
       if (lane == 0) {
@@ -664,155 +698,170 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
     issue_next();
 
     // ---------------------------------------------------- rows of the block
+    // nb rows of the current triangle, then (ntri > 0) each following whole
+    // triangle in turn, at consecutive positions of the buffer
     const ST *bp = reinterpret_cast<const ST *>(buf) + ((dsc.y >> 6) & 15);
-    // lane i holds row i: its head, alpha and coefficients
-    const bool live = lane < nb;
-    const int ci = min(c + lane, n - 1);
-    const N ac = alpha_at(ci);
-    const bool first = ci == b;
-    const N coef = first ? cAf : cA;
-    const int rowend = live ? (L0 - 1) + lane * L0 - ((lane * (lane + 1)) >> 1) : L0 - 1;
-    const int rsl = live ? L0 - lane - 1 : 0;
-    const CT hv = ld_elem<ST, CT>(bp + (rowend - rsl));
-    {
-      // rows past the block's end read row 0's (finite) entries with a zero
-      // coefficient, so the unmasked chunks stay harmless
-      const N cfi = live ? coef * ac : mk<CT, D>(CT(0), CT(0));
-      RowInfo<CT> rw;
-      rw.cf_v = cfi.v;
-      rw.cf_d = cfi.d;
-      rw.rowend = rowend;
-      rw.sl = rsl;
-      rinfo[lane] = rw;
-    }
-    __syncwarp();
-    N s = mk<CT, D>(CT(0), CT(0));  // the dot of row `lane`
-    for (int r = 0; r < nb; r += 4) {
-      // four rows at a time: their lengths differ by at most 3, so the chunk
-      // count of the longest serves all four; only its top two chunks can run
-      // past a row's end and need masks
-      N cf[4], dot[4];
-      int sl[4];
-      const ST *prow[4];
-      CT xa[4], xb[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const RowInfo<CT> rw = rinfo[r + i];
-        cf[i] = mk<CT, D>(rw.cf_v, rw.cf_d);
-        sl[i] = rw.sl;
-        prow[i] = bp + (rw.rowend - lane);
-        dot[i] = mk<CT, D>(CT(0), CT(0));
-      }
-      // enter at the top chunk (two masked chunks), continue down the
-      // unmasked chain to chunk 0
-      switch ((sl[0] + 31) >> 5) {
-        case 1: quad_load<0, NC>(prow, sl, lane, xa); quad_step<0, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto chunks_done;
-        case 2: quad_load<1, NC>(prow, sl, lane, xb); quad_step<1, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<0, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto chunks_done;
-        case 3: quad_load<2, NC>(prow, sl, lane, xa); quad_step<2, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<1, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_0;
-        case 4: quad_load<3, NC>(prow, sl, lane, xb); quad_step<3, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<2, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_1;
-        case 5: quad_load<4, NC>(prow, sl, lane, xa); quad_step<4, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<3, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_2;
-        case 6: quad_load<5, NC>(prow, sl, lane, xb); quad_step<5, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<4, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_3;
-        case 7: quad_load<6, NC>(prow, sl, lane, xa); quad_step<6, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<5, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_4;
-        case 8: quad_load<7, NC>(prow, sl, lane, xb); quad_step<7, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<6, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_5;
-        case 9: quad_load<8, NC>(prow, sl, lane, xa); quad_step<8, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<7, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_6;
-        case 10: quad_load<9, NC>(prow, sl, lane, xb); quad_step<9, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<8, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_7;
-        case 11: quad_load<10, NC>(prow, sl, lane, xa); quad_step<10, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<9, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_8;
-        case 12: quad_load<11, NC>(prow, sl, lane, xb); quad_step<11, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<10, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_9;
-        case 13: quad_load<12, NC>(prow, sl, lane, xa); quad_step<12, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<11, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_10;
-        case 14: quad_load<13, NC>(prow, sl, lane, xb); quad_step<13, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<12, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_11;
-        case 15: quad_load<14, NC>(prow, sl, lane, xa); quad_step<14, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<13, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_12;
-        case 16: quad_load<15, NC>(prow, sl, lane, xb); quad_step<15, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<14, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_13;
-        case 17: quad_load<16, NC>(prow, sl, lane, xa); quad_step<16, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<15, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_14;
-        case 18: quad_load<17, NC>(prow, sl, lane, xb); quad_step<17, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<16, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_15;
-        case 19: quad_load<18, NC>(prow, sl, lane, xa); quad_step<18, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<17, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_16;
-        case 20: quad_load<19, NC>(prow, sl, lane, xb); quad_step<19, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<18, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_17;
-        case 21: quad_load<20, NC>(prow, sl, lane, xa); quad_step<20, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<19, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_18;
-        case 22: quad_load<21, NC>(prow, sl, lane, xb); quad_step<21, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<20, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_19;
-        case 23: quad_load<22, NC>(prow, sl, lane, xa); quad_step<22, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<21, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_20;
-        case 24: quad_load<23, NC>(prow, sl, lane, xb); quad_step<23, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<22, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_21;
-        case 25: quad_load<24, NC>(prow, sl, lane, xa); quad_step<24, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<23, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_22;
-        case 26: quad_load<25, NC>(prow, sl, lane, xb); quad_step<25, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<24, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_23;
-        case 27: quad_load<26, NC>(prow, sl, lane, xa); quad_step<26, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<25, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_24;
-        case 28: quad_load<27, NC>(prow, sl, lane, xb); quad_step<27, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<26, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_25;
-        case 29: quad_load<28, NC>(prow, sl, lane, xa); quad_step<28, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<27, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_26;
-        case 30: quad_load<29, NC>(prow, sl, lane, xb); quad_step<29, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<28, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_27;
-        case 31: quad_load<30, NC>(prow, sl, lane, xa); quad_step<30, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<29, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_28;
-        case 32: quad_load<31, NC>(prow, sl, lane, xb); quad_step<31, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<30, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_29;
-        default: goto chunks_done;
-      }
-    full_29: quad_step<29, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
-    full_28: quad_step<28, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
-    full_27: quad_step<27, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
-    full_26: quad_step<26, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
-    full_25: quad_step<25, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
-    full_24: quad_step<24, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
-    full_23: quad_step<23, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
-    full_22: quad_step<22, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
-    full_21: quad_step<21, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
-    full_20: quad_step<20, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
-    full_19: quad_step<19, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
-    full_18: quad_step<18, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
-    full_17: quad_step<17, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
-    full_16: quad_step<16, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
-    full_15: quad_step<15, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
-    full_14: quad_step<14, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
-    full_13: quad_step<13, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
-    full_12: quad_step<12, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
-    full_11: quad_step<11, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
-    full_10: quad_step<10, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
-    full_9: quad_step<9, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
-    full_8: quad_step<8, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
-    full_7: quad_step<7, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
-    full_6: quad_step<6, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
-    full_5: quad_step<5, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
-    full_4: quad_step<4, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
-    full_3: quad_step<3, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
-    full_2: quad_step<2, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
-    full_1: quad_step<1, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
-    full_0: quad_step<0, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
-    chunks_done:;
+    bool stop = false;
+    for (;;) {
+      const int L0 = n - c;
+      __syncwarp();
+      // lane i holds row i: its head, alpha and coefficients
+      const bool live = lane < nb;
+      const int ci = min(c + lane, n - 1);
+      const N ac = alpha_at(ci);
+      const bool first = ci == b;
+      const N coef = first ? cAf : cA;
+      const int rowend = live ? (L0 - 1) + lane * L0 - ((lane * (lane + 1)) >> 1) : L0 - 1;
+      const int rsl = live ? L0 - lane - 1 : 0;
+      const CT hv = ld_elem<ST, CT>(bp + (rowend - rsl));
       {
-        // butterfly over the lanes: after it lane l holds the dot of row
-        // r + 2 (l >> 4 & 1) + (l >> 3 & 1); row r + i then moves to lane r + i
-        const bool hi = (lane & 16) != 0, b8 = (lane & 8) != 0;
-        const N k0 = (hi ? dot[2] : dot[0]) + shfl_xor(hi ? dot[0] : dot[2], 16);
-        const N k1 = (hi ? dot[3] : dot[1]) + shfl_xor(hi ? dot[1] : dot[3], 16);
-        N k = (b8 ? k1 : k0) + shfl_xor(b8 ? k0 : k1, 8);
-        k = k + shfl_xor(k, 4);
-        k = k + shfl_xor(k, 2);
-        k = k + shfl_xor(k, 1);
-        k = shfl_idx(k, ((lane & 2) << 3) | ((lane & 1) << 3));
-        if ((lane & ~3) == r) s = k;
+        // rows past the block's end read row 0's (finite) entries with a zero
+        // coefficient, so the unmasked chunks stay harmless
+        const N cfi = live ? coef * ac : mk<CT, D>(CT(0), CT(0));
+        RowInfo<CT> rw;
+        rw.cf_v = cfi.v;
+        rw.cf_d = cfi.d;
+        rw.rowend = rowend;
+        rw.sl = rsl;
+        rinfo[lane] = rw;
       }
-    }
-
-    // ---------------------------------------------------- row epilogue
-    if (live) {
-      const CT cnt = first ? CT(kb + 1) : CT(1);
-      const N Rf = s + scale(hv * (first ? inv_first : CT(0.5)), ac);
-      const N gadd = coef * (scale(hv, ac) + scale(cnt, s));
-      g_v[ci] += gadd.v;
-      if (D) g_d[ci] += gadd.d;
-      const N tadd = scale(first ? Mf : Mprime, ac * Rf);
-      if (first) Tfirst = Tfirst + tadd;
-      else Trest = Trest + tadd;
-    }
-
-    // ---------------------------------------------------- advance
-    c += nb;
-    if (c == n) {
-      flush_triangle();
-      open = false;
-      if (!(dsc.y & kDescLast)) {
-        if (m > 2 && next_sorted(m - 2, n, Q)) {
-          c = Q[m - 3];
-          setup_triangle();
-          open = true;
-        } else {
-          break;
+      __syncwarp();
+      N s = mk<CT, D>(CT(0), CT(0));  // the dot of row `lane`
+      for (int r = 0; r < nb; r += 4) {
+        // four rows at a time: their lengths differ by at most 3, so the chunk
+        // count of the longest serves all four; only its top two chunks can run
+        // past a row's end and need masks
+        N cf[4], dot[4];
+        int sl[4];
+        const ST *prow[4];
+        CT xa[4], xb[4];
+  #pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const RowInfo<CT> rw = rinfo[r + i];
+          cf[i] = mk<CT, D>(rw.cf_v, rw.cf_d);
+          sl[i] = rw.sl;
+          prow[i] = bp + (rw.rowend - lane);
+          dot[i] = mk<CT, D>(CT(0), CT(0));
+        }
+        // enter at the top chunk (two masked chunks), continue down the
+        // unmasked chain to chunk 0
+        switch ((sl[0] + 31) >> 5) {
+          case 1: quad_load<0, NC>(prow, sl, lane, xa); quad_step<0, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto chunks_done;
+          case 2: quad_load<1, NC>(prow, sl, lane, xb); quad_step<1, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<0, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto chunks_done;
+          case 3: quad_load<2, NC>(prow, sl, lane, xa); quad_step<2, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<1, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_0;
+          case 4: quad_load<3, NC>(prow, sl, lane, xb); quad_step<3, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<2, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_1;
+          case 5: quad_load<4, NC>(prow, sl, lane, xa); quad_step<4, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<3, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_2;
+          case 6: quad_load<5, NC>(prow, sl, lane, xb); quad_step<5, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<4, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_3;
+          case 7: quad_load<6, NC>(prow, sl, lane, xa); quad_step<6, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<5, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_4;
+          case 8: quad_load<7, NC>(prow, sl, lane, xb); quad_step<7, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<6, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_5;
+          case 9: quad_load<8, NC>(prow, sl, lane, xa); quad_step<8, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<7, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_6;
+          case 10: quad_load<9, NC>(prow, sl, lane, xb); quad_step<9, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<8, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_7;
+          case 11: quad_load<10, NC>(prow, sl, lane, xa); quad_step<10, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<9, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_8;
+          case 12: quad_load<11, NC>(prow, sl, lane, xb); quad_step<11, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<10, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_9;
+          case 13: quad_load<12, NC>(prow, sl, lane, xa); quad_step<12, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<11, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_10;
+          case 14: quad_load<13, NC>(prow, sl, lane, xb); quad_step<13, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<12, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_11;
+          case 15: quad_load<14, NC>(prow, sl, lane, xa); quad_step<14, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<13, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_12;
+          case 16: quad_load<15, NC>(prow, sl, lane, xb); quad_step<15, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<14, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_13;
+          case 17: quad_load<16, NC>(prow, sl, lane, xa); quad_step<16, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<15, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_14;
+          case 18: quad_load<17, NC>(prow, sl, lane, xb); quad_step<17, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<16, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_15;
+          case 19: quad_load<18, NC>(prow, sl, lane, xa); quad_step<18, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<17, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_16;
+          case 20: quad_load<19, NC>(prow, sl, lane, xb); quad_step<19, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<18, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_17;
+          case 21: quad_load<20, NC>(prow, sl, lane, xa); quad_step<20, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<19, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_18;
+          case 22: quad_load<21, NC>(prow, sl, lane, xb); quad_step<21, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<20, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_19;
+          case 23: quad_load<22, NC>(prow, sl, lane, xa); quad_step<22, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<21, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_20;
+          case 24: quad_load<23, NC>(prow, sl, lane, xb); quad_step<23, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<22, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_21;
+          case 25: quad_load<24, NC>(prow, sl, lane, xa); quad_step<24, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<23, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_22;
+          case 26: quad_load<25, NC>(prow, sl, lane, xb); quad_step<25, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<24, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_23;
+          case 27: quad_load<26, NC>(prow, sl, lane, xa); quad_step<26, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<25, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_24;
+          case 28: quad_load<27, NC>(prow, sl, lane, xb); quad_step<27, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<26, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_25;
+          case 29: quad_load<28, NC>(prow, sl, lane, xa); quad_step<28, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<27, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_26;
+          case 30: quad_load<29, NC>(prow, sl, lane, xb); quad_step<29, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<28, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_27;
+          case 31: quad_load<30, NC>(prow, sl, lane, xa); quad_step<30, true>(acc, dot, ar, prow, sl, lane, cf, xa, xb); quad_step<29, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa); goto full_28;
+          case 32: quad_load<31, NC>(prow, sl, lane, xb); quad_step<31, true>(acc, dot, ar, prow, sl, lane, cf, xb, xa); quad_step<30, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb); goto full_29;
+          default: goto chunks_done;
+        }
+      full_29: quad_step<29, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+      full_28: quad_step<28, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+      full_27: quad_step<27, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+      full_26: quad_step<26, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+      full_25: quad_step<25, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+      full_24: quad_step<24, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+      full_23: quad_step<23, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+      full_22: quad_step<22, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+      full_21: quad_step<21, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+      full_20: quad_step<20, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+      full_19: quad_step<19, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+      full_18: quad_step<18, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+      full_17: quad_step<17, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+      full_16: quad_step<16, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+      full_15: quad_step<15, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+      full_14: quad_step<14, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+      full_13: quad_step<13, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+      full_12: quad_step<12, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+      full_11: quad_step<11, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+      full_10: quad_step<10, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+      full_9: quad_step<9, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+      full_8: quad_step<8, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+      full_7: quad_step<7, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+      full_6: quad_step<6, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+      full_5: quad_step<5, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+      full_4: quad_step<4, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+      full_3: quad_step<3, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+      full_2: quad_step<2, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+      full_1: quad_step<1, false>(acc, dot, ar, prow, sl, lane, cf, xb, xa);
+      full_0: quad_step<0, false>(acc, dot, ar, prow, sl, lane, cf, xa, xb);
+      chunks_done:;
+        {
+          // butterfly over the lanes: after it lane l holds the dot of row
+          // r + 2 (l >> 4 & 1) + (l >> 3 & 1); row r + i then moves to lane r + i
+          const bool hi = (lane & 16) != 0, b8 = (lane & 8) != 0;
+          const N k0 = (hi ? dot[2] : dot[0]) + shfl_xor(hi ? dot[0] : dot[2], 16);
+          const N k1 = (hi ? dot[3] : dot[1]) + shfl_xor(hi ? dot[1] : dot[3], 16);
+          N k = (b8 ? k1 : k0) + shfl_xor(b8 ? k0 : k1, 8);
+          k = k + shfl_xor(k, 4);
+          k = k + shfl_xor(k, 2);
+          k = k + shfl_xor(k, 1);
+          k = shfl_idx(k, ((lane & 2) << 3) | ((lane & 1) << 3));
+          if ((lane & ~3) == r) s = k;
         }
       }
+
+      // ---------------------------------------------------- row epilogue
+      if (live) {
+        const CT cnt = first ? CT(kb + 1) : CT(1);
+        const N Rf = s + scale(hv * (first ? inv_first : CT(0.5)), ac);
+        const N gadd = coef * (scale(hv, ac) + scale(cnt, s));
+        g_v[ci] += gadd.v;
+        if (D) g_d[ci] += gadd.d;
+        const N tadd = scale(first ? Mf : Mprime, ac * Rf);
+        if (first) Tfirst = Tfirst + tadd;
+        else Trest = Trest + tadd;
+      }
+
+      // ---------------------------------------------------- advance
+      c += nb;
+      if (c == n) {
+        flush_triangle();
+        open = false;
+        // the block's last triangle may end its piece; the next piece then
+        // restarts the cursor from its plan record
+        if (ntri > 0 || !(dsc.y & kDescLast)) {
+          if (m > 2 && next_sorted(m - 2, n, Q)) {
+            c = Q[m - 3];
+            setup_triangle();
+            open = true;
+          } else {
+            stop = true;
+            break;
+          }
+        }
+      }
+      if (!kMultiTri || ntri == 0) break;
+      --ntri;
+      bp += nb * L0 - ((nb * (nb - 1)) >> 1);
+      nb = n - c;  // the next triangle, whole
     }
+    if (stop) break;
   }
   if (open) flush_triangle();
   // drain copies still in flight before the block can exit
