@@ -414,10 +414,11 @@ template <typename ST, typename CT, bool D, int NC>
 __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(KParams p) {
   using N = Nm<CT, D>;
   constexpr int ES = sizeof(ST);
-  // blocks of several whole triangles (n <= 256 only: at larger n the
-  // triangles of at most 32 rows hold a negligible share of the entries, and
-  // the loop costs the wide instances registers)
-  constexpr bool kMultiTri = NC <= 8;
+  // blocks of several whole triangles and the cached step between triangles
+  // (n <= 256, n <= 128 for FP64: at larger n the triangles of at most 32 rows
+  // hold a negligible share of the entries, and both cost the wide instances
+  // registers)
+  constexpr bool kMultiTri = NC <= (sizeof(CT) == 8 ? 4 : 8);
   extern __shared__ __align__(128) unsigned char smem[];
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
@@ -600,9 +601,19 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
   N cA = AQ, cAf = AQ;
   N Trest = mk<CT, D>(CT(0), CT(0)), Tfirst = Trest;
   const CT inv_m = CT(1) / CT(m);
+  // Prefix cache for the step between consecutive triangles (P, b) -> (P, b+1)
+  // of one (m-3)-prefix P = (Q_0..Q_{m-4}) (multi-triangle instances): when b
+  // is unique in Q and b < n-1, b+1 is unique in the next triangle too, so M',
+  // M_f and 1/(cnt_Q(b)+2) stay, A_Q = A_P a_{b+1}, and lane l < m-2 keeps its
+  // prefix value, its count and B_{Q,l} without the factor a_b.  Every product
+  // is formed in the order of the full set-up, so both give the same roundings.
+  N AP = mk<CT, D>(CT(1), CT(0));  // product of a over Q_0..Q_{m-4}
+  N BP_l = AP;                     // lane l < m-3: that product without position l
+  int q_l = 0, cnt_l = 0;          // lane l < m-2: Q_l and cnt_Q(Q_l) (0 unless first of its run)
 
   auto setup_triangle = [&]() {
     AQ = mk<CT, D>(CT(1), CT(0));
+    AP = AQ;
     // M' = m! / prod_v cnt_Q(v)!: divide m! by the position of each entry in
     // its run of equal values (every partial quotient is a multinomial
     // coefficient, so each division is exact)
@@ -611,6 +622,7 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
     int run = 0;
     for (int j = 0; j < m - 2; ++j) {
       AQ = AQ * alpha_at(Q[j]);
+      if (j == m - 4) AP = AQ;
       run = (j > 0 && Q[j] == Q[j - 1]) ? run + 1 : 1;
       if (run > 1) mp = exact_div_small(mp, run);
     }
@@ -622,6 +634,29 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
     inv_first = kInvSmall<CT>[kb + 2];      // 1 / (cnt_Q(b) + 2), cnt_Q(b) <= m - 2
     cA = scale(Mprime * inv_m, AQ);
     cAf = scale(Mf * inv_m, AQ);
+    if constexpr (kMultiTri) {
+      if (lane < m - 2) {
+        q_l = Q[lane];
+        int cnt = 0;
+        N B = mk<CT, D>(CT(1), CT(0));
+        for (int j = 0; j < m - 2; ++j) {
+          cnt += (Q[j] == q_l);
+          if (j != lane && j < m - 3) B = B * alpha_at(Q[j]);
+        }
+        cnt_l = (lane == 0 || Q[lane] != Q[lane - 1]) ? cnt : 0;
+        BP_l = B;
+      }
+    }
+  };
+
+  // the next triangle (P, b+1) when b is unique in Q and below n-1
+  auto step_triangle = [&]() {
+    b += 1;
+    Q[m - 3] = b;
+    AQ = AP * alpha_at(b);
+    cA = scale(Mprime * inv_m, AQ);
+    cAf = scale(Mf * inv_m, AQ);
+    if (lane == m - 3) q_l = b;
   };
 
   auto flush_triangle = [&]() {
@@ -632,7 +667,14 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
     N SQ = AQ * T;
     S_v += (double)SQ.v;
     if (D) S_d += (double)SQ.d;
-    if (lane < m - 2 && (lane == 0 || Q[lane] != Q[lane - 1])) {
+    if constexpr (kMultiTri) {
+      if (lane < m - 2 && cnt_l > 0) {
+        const N B = (lane < m - 3) ? BP_l * alpha_at(b) : AP;
+        N add = scale(CT(cnt_l) * inv_m, B * ((q_l == b) ? Tr : T));
+        g_v[q_l] += add.v;
+        if (D) g_d[q_l] += add.d;
+      }
+    } else if (lane < m - 2 && (lane == 0 || Q[lane] != Q[lane - 1])) {
       const int l = Q[lane];
       int cnt = 0;
       N B = mk<CT, D>(CT(1), CT(0));
@@ -846,7 +888,11 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
         // the block's last triangle may end its piece; the next piece then
         // restarts the cursor from its plan record
         if (ntri > 0 || !(dsc.y & kDescLast)) {
-          if (m > 2 && next_sorted(m - 2, n, Q)) {
+          if (kMultiTri && m > 2 && kb == 1 && b < n - 1) {
+            step_triangle();
+            c = b;
+            open = true;
+          } else if (m > 2 && next_sorted(m - 2, n, Q)) {
             c = Q[m - 3];
             setup_triangle();
             open = true;
