@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(256) build_kernel(BParams p) {
   __shared__ int64_t pre[TK_MAX_POINTS + 1];
   __shared__ __align__(16) CT Ys[kKT][kTM];
   __shared__ __align__(16) CT Xs[kKT][kTM];
+  __shared__ CT ws[kKT];
   const int tid = threadIdx.x;
   const int m = p.m, n = p.n, d = p.d;
   const int ngroups = (m == 2) ? 1 : n;
@@ -132,37 +133,29 @@ __global__ void __launch_bounds__(256) build_kernel(BParams p) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = CT(0);
 
-    // 64 rows x 16 features for each of Ys and Xs per stage: 1024 values, 4
-    // per thread, all four at feature kk = tid mod 16, so each thread forms
-    // its own weight w_k = prod_j x_{Q_j, k}.  The next stage's values are
-    // loaded into registers while the current stage's multiply-adds run.
-    const int kk_t = tid & 15;
-    CT xc[4], xd[4], wk;
-    auto fetch = [&](int k0) {
-      const int k = k0 + kk_t;
-      CT w = CT(1);
-      if (k < d)
-        for (int j = 0; j < m - 2; ++j) w *= (CT)p.X[(int64_t)tup[j] * d + k];
-      wk = (k < d) ? w : CT(0);
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int row = (tid + 256 * r) >> 4;
-        const int c = c0 + row, dd = d0 + row;
-        xc[r] = (c < n && k < d) ? (CT)p.X[(int64_t)c * d + k] : CT(0);
-        xd[r] = (dd < n && k < d) ? (CT)p.X[(int64_t)dd * d + k] : CT(0);
-      }
-    };
-    fetch(0);
     for (int k0 = 0; k0 < d; k0 += kKT) {
-      __syncthreads();  // the previous stage's reads of Ys and Xs are done
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int row = (tid + 256 * r) >> 4;
-        Ys[kk_t][row] = xc[r] * wk;
-        Xs[kk_t][row] = xd[r];
+      __syncthreads();
+      if (tid < kKT) {
+        const int k = k0 + tid;
+        CT w = CT(1);
+        if (k < d)
+          for (int j = 0; j < m - 2; ++j) w *= (CT)p.X[(int64_t)tup[j] * d + k];
+        ws[tid] = (k < d) ? w : CT(0);
       }
       __syncthreads();
-      if (k0 + kKT < d) fetch(k0 + kKT);
+      // 64 rows x 16 features for each of Ys and Xs: 1024 values, 4 per thread
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int e = tid + 256 * r;
+        const int row = e >> 4, kk = e & 15;
+        const int k = k0 + kk;
+        const int c = c0 + row, dd = d0 + row;
+        const CT xc = (c < n && k < d) ? (CT)p.X[(int64_t)c * d + k] : CT(0);
+        const CT xd = (dd < n && k < d) ? (CT)p.X[(int64_t)dd * d + k] : CT(0);
+        Ys[kk][row] = xc * ws[kk];
+        Xs[kk][row] = xd;
+      }
+      __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < kKT; ++kk) {
         CT a[4], bv[4];
