@@ -132,6 +132,13 @@ __device__ __forceinline__ void fma_acc(Nm<T, D> &acc, T x, Nm<T, D> a) {
   acc.v = fmx(x, a.v, acc.v);
   if (D) acc.d = fmx(x, a.d, acc.d);
 }
+// The column accumulators of g: the dual pass returns only the derivative
+// part (the Hessian-vector product), so its value part is not accumulated.
+template <typename T, bool D>
+__device__ __forceinline__ void fma_col(Nm<T, D> &acc, T x, Nm<T, D> a) {
+  if (D) acc.d = fmx(x, a.d, acc.d);
+  else acc.v = fmx(x, a.v, acc.v);
+}
 template <typename T, bool D>
 __device__ __forceinline__ Nm<T, D> shfl_xor(Nm<T, D> a, int mask) {
   Nm<T, D> r;
@@ -288,7 +295,7 @@ __device__ __forceinline__ void quad_step(Nm<CT, D> (&acc)[NC], Nm<CT, D> (&dot)
   if constexpr (K < NC) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      fma_acc(acc[K], xc[i], cf[i]);
+      fma_col(acc[K], xc[i], cf[i]);
       fma_acc(dot[i], xc[i], ar[K]);
     }
   }
@@ -665,14 +672,14 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
     N Tf = warp_sum(Tfirst);
     N T = Tr + Tf;
     N SQ = AQ * T;
-    S_v += (double)SQ.v;
     if (D) S_d += (double)SQ.d;
+    else S_v += (double)SQ.v;
     if constexpr (kMultiTri) {
       if (lane < m - 2 && cnt_l > 0) {
         const N B = (lane < m - 3) ? BP_l * alpha_at(b) : AP;
         N add = scale(CT(cnt_l) * inv_m, B * ((q_l == b) ? Tr : T));
-        g_v[q_l] += add.v;
         if (D) g_d[q_l] += add.d;
+        else g_v[q_l] += add.v;
       }
     } else if (lane < m - 2 && (lane == 0 || Q[lane] != Q[lane - 1])) {
       const int l = Q[lane];
@@ -683,16 +690,16 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
         if (j != lane) B = B * alpha_at(Q[j]);
       }
       N add = scale(CT(cnt) * inv_m, B * ((l == b) ? Tr : T));
-      g_v[l] += add.v;
       if (D) g_d[l] += add.d;
+      else g_v[l] += add.v;
     }
     __syncwarp();
 #pragma unroll
     for (int k = 0; k < NC; ++k) {
       const int e = 32 * k + lane;
       if (e < n) {
-        g_v[n - 1 - e] += acc[k].v;
         if (D) g_d[n - 1 - e] += acc[k].d;
+        else g_v[n - 1 - e] += acc[k].v;
       }
       acc[k] = mk<CT, D>(CT(0), CT(0));
     }
@@ -873,8 +880,8 @@ __global__ void __launch_bounds__(max_threads<CT, D, NC>(), 1) contract_kernel(K
         const CT cnt = first ? CT(kb + 1) : CT(1);
         const N Rf = s + scale(hv * (first ? inv_first : CT(0.5)), ac);
         const N gadd = coef * (scale(hv, ac) + scale(cnt, s));
-        g_v[ci] += gadd.v;
         if (D) g_d[ci] += gadd.d;
+        else g_v[ci] += gadd.v;
         const N tadd = scale(first ? Mf : Mprime, ac * Rf);
         if (first) Tfirst = Tfirst + tadd;
         else Trest = Trest + tadd;
