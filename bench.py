@@ -754,7 +754,8 @@ def run_case(args) -> None:
         call()
     e1.record()
     e1.synchronize()
-    print(json.dumps({"case": args.case, "B": args.B if args.case != "hessian" else 1, "tensor_cores": args.tc,
+    batched = args.case == "batched_pass"
+    print(json.dumps({"case": args.case, "B": args.B if batched else 1, "tensor_cores": args.tc if batched else None,
                       "ms_per_call": e0.elapsed_time(e1) / 3, "entries": int(K.numel()),
                       "TB_per_s": K.numel() * K.element_size() / (e0.elapsed_time(e1) / 3) / 1e9}), flush=True)
 
